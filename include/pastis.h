@@ -1,0 +1,223 @@
+/*
+ * pastis.h - C ABI of the GB300 (sm_103a) PASTIS hot path.
+ *
+ * PASTIS (Selvitopi, Ekanayake, Guidi, Pavlopoulos, Azad, Buluc; SC20, arXiv
+ * 2009.14467) builds a protein similarity graph G = (V, E): V is the set of
+ * sequences, and an edge joins two sequences whose alignment passes the similarity
+ * thresholds (Sec. II).  The hot path this library runs on one GPU:
+ *
+ *   pastis_encode            letters -> residue codes                (Sec. V-B)
+ *   pastis_build_kmers       A (sequence x k-mer) in CSR and CSC      (Sec. IV-A, V-B)
+ *   pastis_substitute_kmers  rows of S: m nearest substitute k-mers   (Sec. IV-B, Alg. 1-3)
+ *   pastis_overlap_spgemm    candidates B = A A^T or (A S) A^T        (Sec. IV-A, IV-C)
+ *   pastis_align_pairs       Smith-Waterman or x-drop alignment       (Sec. IV-E)
+ *   pastis_filter_edges      ANI / coverage filter -> edges           (Sec. IV-F, VI-B)
+ *
+ * Conventions shared by every call:
+ *  - Every pointer named d_* is DEVICE memory owned by the caller; h_* is host
+ *    memory.  The library never frees caller memory.  It owns only the workspace
+ *    inside a context (grown on demand with cudaMalloc, freed by
+ *    pastis_ctx_destroy).
+ *  - Work is enqueued on the context's stream.  A call that reports a size to the
+ *    host (nnz_out, n_out) synchronises that stream once; the others do not.
+ *  - A call that writes a variable-sized result takes `capacity` (records
+ *    available at d_out).  If the result does not fit it returns
+ *    PASTIS_ERR_CAPACITY, stores the needed count in *n_out and writes nothing to
+ *    d_out; calling again with a large enough buffer and the same inputs copies the
+ *    kept result without recomputing it.
+ *  - No exception crosses the ABI; failures are status codes.  A context is used
+ *    by one host thread at a time.
+ *  - Residue codes are 0..23 in the order ARNDCQEGHILKMFPSTWYVBZX* (Sec. V-B).
+ *    Sequences are concatenated; offsets has n+1 entries, non-decreasing, and a
+ *    sequence is at most 65535 residues long (positions are stored as uint16).
+ *  - k-mer codes: id = sum_t code(s[p+t]) * 24^(k-1-t), the leftmost residue most
+ *    significant (Sec. V-B; RCQ -> 677).  1 <= k <= 6, so ids fit in 32 bits.
+ */
+#ifndef PASTIS_H
+#define PASTIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pastis_status;
+enum {
+    PASTIS_OK = 0,
+    PASTIS_ERR_INVALID_ARG = 1,      /* a null pointer, a size or a parameter out of range */
+    PASTIS_ERR_INVALID_RESIDUE = 2,  /* pastis_encode met a byte outside the alphabet      */
+    PASTIS_ERR_CAPACITY = 3,         /* d_out too small; *n_out holds the needed count     */
+    PASTIS_ERR_OUT_OF_MEMORY = 4,    /* workspace allocation failed                        */
+    PASTIS_ERR_CUDA = 5,             /* a CUDA runtime call failed                          */
+    PASTIS_ERR_TIMEOUT = 6,          /* a bounded device-side wait ran out                 */
+    PASTIS_ERR_UNSUPPORTED = 7,      /* a valid request this build does not implement      */
+    PASTIS_ERR_INTERNAL = 8          /* a device-side consistency check failed             */
+};
+
+/* Alignment modes (Sec. IV-E). */
+enum { PASTIS_SW = 0, PASTIS_XD = 1 };
+
+/* Parameters of the method (Sec. VI: k = 6, BLOSUM62, gap open 11, extension 1,
+ * x-drop 49, common-k-mer threshold; Sec. IV-F: ANI 30%, coverage 70%).          */
+typedef struct pastis_params {
+    int32_t k;            /* k-mer length, 1..6                                          */
+    int32_t m_subs;       /* substitute k-mers per k-mer, 0 = exact matching, <= 128     */
+    int32_t min_shared;   /* candidate iff it shares >= min_shared k-mers; the paper's  */
+                          /* "common k-mer threshold t" drops <= t, i.e. min_shared=t+1 */
+    int32_t mode;         /* PASTIS_SW or PASTIS_XD                                      */
+    int32_t xdrop;        /* X of the x-drop extension (49)                              */
+    int32_t gap_open;     /* a gap of length L costs gap_open + (L-1)*gap_extend         */
+    int32_t gap_extend;
+    int32_t ani_min_pct;  /* keep iff 100*ident >= ani_min_pct*cols                     */
+    int32_t cov_min_pct;  /* and 100*span(shorter) >= cov_min_pct*len(shorter)          */
+    int8_t matrix[24 * 24]; /* substitution scores, row-major in alphabet order; must be */
+                            /* symmetric, entries in [-64, 63]                            */
+} pastis_params;
+
+/* Candidate pair (an entry of B, Sec. IV-A Fig. 3): i < j.  count is the number of
+ * shared k-mers (with substitutes: of the orientation kept by symmetrization).  The
+ * seeds are the shared k-mers with the two smallest codes, ascending: qpos[s] is the
+ * start in sequence i, tpos[s] in sequence j; seed 1 is 0xFFFF when count == 1. 20 B. */
+typedef struct pastis_cand {
+    int32_t i, j;
+    uint32_t count;
+    uint16_t qpos[2];
+    uint16_t tpos[2];
+} pastis_cand;
+
+/* Alignment of candidate (i, j), i the query (rows), j the target.  Spans are
+ * half-open: [qb, qe) on i and [tb, te) on j; ident = columns with equal residues,
+ * cols = all columns including gap columns.  score == 0 means no positive local
+ * alignment and then every other field is 0.  seed_used is the XD seed kept (0 or
+ * 1); passes is the filter verdict.  20 B.                                          */
+typedef struct pastis_aln {
+    int32_t score;
+    uint16_t qb, qe, tb, te;
+    uint16_t ident, cols;
+    uint8_t seed_used, passes;
+    uint16_t reserved;
+} pastis_aln;
+
+/* Edge of the similarity graph: weight = ANI = ident / cols (IEEE float32 division). */
+typedef struct pastis_edge {
+    int32_t i, j;
+    uint16_t ident, cols;
+    int32_t score;
+    float weight;
+} pastis_edge;
+
+/* The sequence x k-mer matrix A (Sec. IV-A) in two views, all device memory owned by
+ * the caller.  Sizes come from pastis_kmat_sizes().
+ *   CSR (rows = sequences): row_ptr[n_rows+1]; row_code/row_pos[capacity]: the
+ *     distinct k-mers of a row in ascending code order with their smallest start
+ *     position (a k-mer repeated in one sequence keeps its first occurrence).
+ *   CSC (columns = k-mer codes, dense over all 24^k codes): col_ptr[24^k + 1];
+ *     col_seq/col_pos[capacity]: for each code its sequences ascending with the
+ *     start position (the posting lists of A^T).
+ * pastis_build_kmers fills every array and sets nnz; the other fields are inputs. */
+typedef struct pastis_kmat {
+    int32_t n_rows;
+    int32_t k;
+    int64_t capacity;
+    int64_t nnz;
+    int64_t *row_ptr;
+    uint32_t *row_code;
+    uint16_t *row_pos;
+    uint32_t *col_ptr;
+    int32_t *col_seq;
+    uint16_t *col_pos;
+} pastis_kmat;
+
+typedef struct pastis_ctx pastis_ctx;
+
+/* ---- context ------------------------------------------------------------------ */
+
+/* Creates a context on `device` that enqueues on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream).  The stream must outlive the context.              */
+pastis_status pastis_ctx_create(pastis_ctx **ctx, int device, void *stream);
+pastis_status pastis_ctx_destroy(pastis_ctx *ctx);
+const char *pastis_status_string(pastis_status s);
+/* Bytes of workspace the context holds now. */
+int64_t pastis_ctx_workspace_bytes(const pastis_ctx *ctx);
+/* Kernel launches the context has issued since creation (for accounting). */
+int64_t pastis_ctx_launch_count(const pastis_ctx *ctx);
+
+/* ---- a1: encode (Sec. V-B) ---------------------------------------------------- */
+
+/* d_ascii[n_bytes] letters -> d_codes[n_bytes] codes 0..23.  Any byte outside the
+ * 24 upper-case letters of the alphabet gives PASTIS_ERR_INVALID_RESIDUE, and
+ * *bad_index (if not NULL) receives the first offending index.  Synchronises.     */
+pastis_status pastis_encode(pastis_ctx *ctx, const uint8_t *d_ascii, int64_t n_bytes,
+                            uint8_t *d_codes, int64_t *bad_index);
+
+/* ---- a2-a3: k-mers and A (Sec. IV-A, Sec. V-B) --------------------------------- */
+
+/* Sizes to allocate for A over n sequences with R residues in total: capacity is the
+ * number of (row, k-mer) entries that can occur (R - n*(k-1), at least 0) and
+ * col_ptr_len = 24^k + 1.                                                          */
+pastis_status pastis_kmat_sizes(int32_t n, int64_t total_residues, int32_t k,
+                                int64_t *capacity, int64_t *col_ptr_len);
+
+/* Builds A from d_codes/d_offsets (n sequences) with a device radix sort: CSR
+ * rows, then CSC posting lists.  A->n_rows, A->k, A->capacity and the array
+ * pointers are inputs; A->nnz and *nnz_out receive the entry count.  Synchronises. */
+pastis_status pastis_build_kmers(pastis_ctx *ctx, const uint8_t *d_codes,
+                                 const int64_t *d_offsets, int32_t n, int32_t k,
+                                 pastis_kmat *A, int64_t *nnz_out);
+
+/* ---- a4: substitute k-mers (Sec. IV-B, Alg. 1-3) -------------------------------- */
+
+/* For each of n_roots k-mer codes r, row r of S: d_sub_code[r*(m+1) + 0] = r with
+ * distance 0, then the m k-mers q != r nearest to r, ascending by (distance, code).
+ * distance(r, q) = sum_t (M[r_t][r_t] - M[r_t][q_t]) (the expense matrix E of
+ * Sec. IV-B; not symmetric).  Ties at equal distance take the smaller code.        */
+pastis_status pastis_substitute_kmers(pastis_ctx *ctx, const uint32_t *d_roots,
+                                      int64_t n_roots, const pastis_params *params,
+                                      uint32_t *d_sub_code, int32_t *d_sub_dist);
+
+/* ---- a5-a7: candidate discovery (Sec. IV-A, IV-C) ------------------------------ */
+
+/* Candidates i < j of the overlap product.  params->m_subs == 0: B = A A^T with the
+ * semiring that counts shared k-mers and keeps two seeds (Sec. IV-A).  m_subs > 0:
+ * S is formed for the k-mers present, AS(i, s) keeps the start of the k-mer of i
+ * nearest to s (smaller start on ties), both orientations (AS)_i.A_j and (AS)_j.A_i
+ * are formed, and the pair keeps the orientation sharing more (i->j on ties) --
+ * symmetrization (Sec. VI-A).  Pairs with count < min_shared are dropped.  Output
+ * sorted by (i, j).  Synchronises.                                                   */
+pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kmat *A,
+                                    const pastis_params *params, pastis_cand *d_out,
+                                    int64_t capacity, int64_t *n_out);
+
+/* ---- a8-a9: alignment (Sec. IV-E) ---------------------------------------------- */
+
+/* One record per candidate, d_out[n_pairs].
+ * PASTIS_SW: Smith-Waterman, affine gaps, seeds ignored.  The end is the first
+ *   maximum in row-major order (rows = residues of i); the alignment is the one a
+ *   traceback from it selects when it prefers diagonal > vertical gap > horizontal
+ *   gap in H, and gap open over gap extension.
+ * PASTIS_XD: from each seed, seed score plus gapped x-drop extensions to the right
+ *   and to the left (antidiagonal order; a cell dies when H < best - xdrop); among
+ *   the seeds whose alignment passes the filter the higher score (first seed on
+ *   ties) is kept, otherwise the best score with passes = 0.
+ * d_cells (optional, device int64) accumulates the DP cells computed.             */
+pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_codes,
+                                 const int64_t *d_offsets, const pastis_cand *d_pairs,
+                                 int64_t n_pairs, const pastis_params *params,
+                                 pastis_aln *d_out, int64_t *d_cells);
+
+/* ---- a10: similarity filter (Sec. IV-F, VI-B) ----------------------------------- */
+
+/* Keeps pair p iff cols > 0, 100*ident >= ani*cols and 100*span >= cov*len, span and
+ * len taken on the shorter sequence (i on equal lengths).  Edges keep pair order.
+ * Synchronises.                                                                     */
+pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets,
+                                  const pastis_cand *d_pairs, const pastis_aln *d_alns,
+                                  int64_t n_pairs, const pastis_params *params,
+                                  pastis_edge *d_out, int64_t capacity, int64_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PASTIS_H */
