@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the PASTIS hot path on GB300: edges/s of the whole path a1..a10.
+
+One step = encode -> k-mer matrix A -> substitute k-mers S -> (A S) A^T candidates with
+symmetrization -> Smith-Waterman of every candidate -> ANI/coverage filter, over the
+whole synthetic protein set, inputs resident in HBM.  The default workload is the
+100,000-protein planted-family set with 25 substitute k-mers and exact int32 SW.
+
+Multi-GPU: the all-vs-all of one set is not split here; each rank runs an independent
+set of the same recipe (seed + rank), so per-GPU work is fixed ("weak" scaling) and
+value = edges of all ranks / the slowest rank's time.
+
+`--impl reference` times the CPU oracle (oracle/) on host cores on bounded samples of
+the same workload instead (the project's reference arm; no GPU work).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "edges/s (whole path: k-mers, A.S.A^T candidates, SW alignment, ANI/coverage filter)"
+UNIT = "edges/s"
+OPS_PER_CELL = 11          # int32 lane-ops per SW cell: E 3, F 3, H 4, running best 1
+INT_LANES_PER_SM = 128     # int32 lanes per SM per clock
+N_SM = 152
+
+WORKLOADS = {
+    "zipf_100k_s25_sw": dict(n=100_000, m=25, mode=0, desc=(
+        "100,000 proteins: 10,000 Zipf(1.5, 1-200) families (80%) + 20% singletons, "
+        "lengths log-normal(median 300) clipped 50-1000, 30% BLOSUM62 substitutions + 5% indels; "
+        "k=6 with 25 substitute k-mers (C = A S A^T, symmetrized), min_shared 1, "
+        "SW int32 BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
+    "zipf_20k_s25_sw": dict(n=20_000, m=25, mode=0, desc="20,000 proteins, same recipe (smaller stand-in)"),
+    "families_1k_sw": dict(n=1000, m=0, mode=0, desc=(
+        "1,000 proteins = 100 families x 10, k=6 exact, SW int32, ANI 30 / cov 70")),
+}
+
+
+def make_set(name, seed_offset=0):
+    w = WORKLOADS[name]
+    if name.startswith("families_1k"):
+        return synth.families_1k(seed=1 + seed_offset)
+    return synth.zipf_100k(seed=2 + seed_offset, n=w["n"])
+
+
+# ---------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]),
+                                 hw=f[5], hwt=f[6], swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------
+def oracle_sample(ps, name, block, rng):
+    """Runs the oracle's whole path on a block of random sequences of the set (every pair
+    in a random block is a uniformly random pair of the set).  Returns (edges, seconds,
+    pairs, cells)."""
+    from oracle import oracle as O
+    w = WORKLOADS[name]
+    ids = np.sort(rng.choice(ps.n, size=min(block, ps.n), replace=False))
+    sub = ps.subset(ids)
+    t0 = time.perf_counter()
+    r = O.run(sub.ascii, sub.offsets, synth.blosum62(), k=6, m=w["m"], mode=w["mode"])
+    dt = time.perf_counter() - t0
+    return len(r["edges"]), dt, len(ids) * (len(ids) - 1) // 2, r["cells"]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    name = args.workload
+    ps = make_set(name)
+    rng = np.random.default_rng(12345)
+    block = args.ref_block
+    for _ in range(args.warmup):
+        oracle_sample(ps, name, block, rng)
+    edges = secs = pairs = cells = 0
+    for _ in range(args.steps):
+        e, dt, p, c = oracle_sample(ps, name, block, rng)
+        edges += e
+        secs += dt
+        pairs += p
+        cells += c
+    value = edges / secs if secs > 0 else 0.0
+    sample = (f"{args.steps} steps, each the oracle's whole path on {block} random sequences of the "
+              f"set ({block * (block - 1) // 2} uniformly random pairs); {pairs} pairs, {cells} SW cells, "
+              f"{edges} edges in {secs:.2f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOADS[name]["desc"], "name": name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gcups": cells / secs / 1e9 if secs > 0 else 0.0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zipf_100k_s25_sw", choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-block", type=int, default=120)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2009_14467_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    name = args.workload
+    w = WORKLOADS[name]
+    ps = make_set(name, seed_offset=rank)
+    mat = synth.blosum62()
+    params = P.Params(matrix=mat, k=6, m_subs=w["m"], mode=w["mode"])
+    ascii_host = torch.from_numpy(ps.ascii).pin_memory()
+    offs_host = torch.from_numpy(ps.offsets).pin_memory()
+    ascii_dev = ascii_host.to(dev)
+    offs_dev = offs_host.to(dev)
+    ctx = P.Context(local_rank)
+    cells = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step():
+        res = P.run(ctx, ascii_dev, offs_dev, params, cells)
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # > L2 (129 MB)
+
+    stream = ctx.stream
+    clock = ClockSampler(local_rank)
+    launches0 = ctx.launches
+    ctx.profile(True)
+    cells.zero_()
+    step_ms = []
+    edges_total = cands_total = 0
+    clock.start()
+    for _ in range(args.steps):
+        flush.fill_(1)                 # evict the previous step's data from L2 (untimed)
+        torch.cuda.synchronize()
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        step_ms.append(ev0.elapsed_time(ev1))
+        edges_total += res["edges"].shape[0]
+        cands_total += res["cands"].shape[0]
+    clk = clock.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launches - launches0
+    total_cells = int(cells.item())
+    my_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([my_ms, edges_total], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        max_ms, all_edges = float(mx[0]), float(t[1])
+    else:
+        max_ms, all_edges = my_ms, float(edges_total)
+    value = all_edges / (max_ms / 1000.0)
+
+    # end to end through the public API from pinned host buffers (H2D + path + D2H)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = []
+    h2d = ascii_host.numel() + offs_host.numel() * 8
+    d2h = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a = ascii_host.to(dev, non_blocking=True)
+        o = offs_host.to(dev, non_blocking=True)
+        r = P.run(ctx, a, o, params)
+        edges_host = r["edges"].to("cpu")
+        torch.cuda.synchronize()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+        d2h = edges_host.numel()
+    e2e_value = edges_host.shape[0] * world / (max(e2e_ms) / 1000.0)
+
+    # roofline of the dominant kernel: SW pass 1 (integer ALU bound)
+    roof = None
+    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    if "sw_pass1" in prof:
+        n_l, ms_l = prof["sw_pass1"]
+        per_launch_cells = total_cells / max(1, n_l)
+        achieved = per_launch_cells * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
+        sm_max = (clk or {}).get("sm_max_mhz", 2070.0) or 2070.0
+        peak = N_SM * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sw_pass1",
+                "peak_note": f"{N_SM} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz (derived, not measured)",
+                "ops_per_cell": OPS_PER_CELL}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(777)
+        e = s = p = c = 0
+        t_start = time.perf_counter()
+        while time.perf_counter() - t_start < 12.0:
+            de, dt, dp, dc = oracle_sample(ps, name, args.ref_block, rng)
+            e += de; s += dt; p += dp; c += dc
+        cpu = {"value": e / s if s > 0 else 0.0, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"oracle whole path on random blocks of {args.ref_block} sequences of the same set: "
+                          f"{p} uniformly random pairs, {c} SW cells, {e} edges in {s:.1f} s on 1 host core")}
+
+    if rank == 0:
+        kernel_ms = {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w["desc"], "name": name, "sequences": ps.n, "residues": int(ps.ascii.size),
+                       "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+            "gcups": total_cells / (my_ms / 1000.0) / 1e9,
+            "candidate_pairs_per_s": cands_total / (my_ms / 1000.0),
+            "candidates_per_step": cands_total // args.steps, "edges_per_step": edges_total // args.steps,
+            "cells_per_step": total_cells // args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "roofline": roof, "dominant_kernel": dominant, "kernel_ms_timed_region": kernel_ms,
+            "clocks": clk, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+        if args.profile_json:
+            with open(args.profile_json, "w") as f:
+                json.dump({"kernels": prof, "steps": args.steps, "cells": total_cells}, f, indent=1)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

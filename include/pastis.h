@@ -23,8 +23,8 @@
  *  - A call that writes a variable-sized result takes `capacity` (records
  *    available at d_out).  If the result does not fit it returns
  *    PASTIS_ERR_CAPACITY, stores the needed count in *n_out and writes nothing to
- *    d_out; calling again with a large enough buffer and the same inputs copies the
- *    kept result without recomputing it.
+ *    d_out; calling again with a large enough buffer and the same inputs gives the
+ *    result (pastis_overlap_spgemm keeps it and copies it without recomputing).
  *  - No exception crosses the ABI; failures are status codes.  A context is used
  *    by one host thread at a time.
  *  - Residue codes are 0..23 in the order ARNDCQEGHILKMFPSTWYVBZX* (Sec. V-B).
@@ -143,6 +143,13 @@ const char *pastis_status_string(pastis_status s);
 int64_t pastis_ctx_workspace_bytes(const pastis_ctx *ctx);
 /* Kernel launches the context has issued since creation (for accounting). */
 int64_t pastis_ctx_launch_count(const pastis_ctx *ctx);
+/* Per-kernel timing: with enable != 0 the context brackets its main kernels with CUDA
+ * events on its stream (this adds event records, not synchronisation).
+ * pastis_ctx_profile_read synchronises the stream and writes one line per kernel name,
+ * "name launches total_ms", into buf (at most len bytes, NUL-terminated); it returns
+ * the bytes written.  Enabling again clears the totals.                             */
+pastis_status pastis_ctx_profile(pastis_ctx *ctx, int enable);
+int32_t pastis_ctx_profile_read(pastis_ctx *ctx, char *buf, int32_t len);
 
 /* ---- a1: encode (Sec. V-B) ---------------------------------------------------- */
 
@@ -154,15 +161,16 @@ pastis_status pastis_encode(pastis_ctx *ctx, const uint8_t *d_ascii, int64_t n_b
 
 /* ---- a2-a3: k-mers and A (Sec. IV-A, Sec. V-B) --------------------------------- */
 
-/* Sizes to allocate for A over n sequences with R residues in total: capacity is the
- * number of (row, k-mer) entries that can occur (R - n*(k-1), at least 0) and
- * col_ptr_len = 24^k + 1.                                                          */
+/* Sizes to allocate for A over n sequences with R residues in total: capacity bounds
+ * the (row, k-mer) entries that can occur (R: each residue starts at most one window)
+ * and col_ptr_len = 24^k + 1.                                                      */
 pastis_status pastis_kmat_sizes(int32_t n, int64_t total_residues, int32_t k,
                                 int64_t *capacity, int64_t *col_ptr_len);
 
 /* Builds A from d_codes/d_offsets (n sequences) with a device radix sort: CSR
  * rows, then CSC posting lists.  A->n_rows, A->k, A->capacity and the array
- * pointers are inputs; A->nnz and *nnz_out receive the entry count.  Synchronises. */
+ * pointers are inputs; A->nnz and *nnz_out receive the entry count.  A capacity
+ * below the number of windows gives PASTIS_ERR_CAPACITY.  Synchronises.            */
 pastis_status pastis_build_kmers(pastis_ctx *ctx, const uint8_t *d_codes,
                                  const int64_t *d_offsets, int32_t n, int32_t k,
                                  pastis_kmat *A, int64_t *nnz_out);
@@ -201,18 +209,22 @@ pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kmat *A,
  *   and to the left (antidiagonal order; a cell dies when H < best - xdrop); among
  *   the seeds whose alignment passes the filter the higher score (first seed on
  *   ties) is kept, otherwise the best score with passes = 0.
- * d_cells (optional, device int64) accumulates the DP cells computed.             */
+ * d_offsets has n_seqs+1 entries; a pair naming a sequence outside [0, n_seqs), or
+ * (XD) a seed that does not fit its sequence, gives PASTIS_ERR_INVALID_ARG before any
+ * alignment runs.  d_cells (optional, device int64) accumulates the DP cells computed
+ * (|q|*|t| per SW pair; computed antidiagonal cells for XD).  Synchronises.         */
 pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_codes,
-                                 const int64_t *d_offsets, const pastis_cand *d_pairs,
-                                 int64_t n_pairs, const pastis_params *params,
-                                 pastis_aln *d_out, int64_t *d_cells);
+                                 const int64_t *d_offsets, int32_t n_seqs,
+                                 const pastis_cand *d_pairs, int64_t n_pairs,
+                                 const pastis_params *params, pastis_aln *d_out,
+                                 int64_t *d_cells);
 
 /* ---- a10: similarity filter (Sec. IV-F, VI-B) ----------------------------------- */
 
 /* Keeps pair p iff cols > 0, 100*ident >= ani*cols and 100*span >= cov*len, span and
  * len taken on the shorter sequence (i on equal lengths).  Edges keep pair order.
  * Synchronises.                                                                     */
-pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets,
+pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets, int32_t n_seqs,
                                   const pastis_cand *d_pairs, const pastis_aln *d_alns,
                                   int64_t n_pairs, const pastis_params *params,
                                   pastis_edge *d_out, int64_t capacity, int64_t *n_out);

@@ -1,0 +1,111 @@
+// Internal declarations shared by the translation units of libpastis (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pastis.h"
+
+#define PASTIS_NSYM 24
+#define PASTIS_MAX_M 128
+#define PASTIS_MAX_LEN 65535
+
+// Workspace slots of a context: one growable device buffer each.
+enum ws_slot {
+    WS_FLAGS = 0,     // small device scalars (error words, counters)
+    WS_SORT_KEYS_A, WS_SORT_KEYS_B, WS_SORT_VALS_A, WS_SORT_VALS_B, WS_SORT_HIST,
+    WS_KMER_TMP,
+    WS_SUB_ROOTS, WS_SUB_CODE, WS_SUB_DIST,
+    WS_AS_ROWPTR, WS_AS_CODE, WS_AS_POS, WS_AS_COLPTR, WS_AS_COLSEQ, WS_AS_COLPOS,
+    WS_AS_TMP_KEY, WS_AS_TMP_VAL,
+    WS_SPG_ROWWORK, WS_SPG_ROWOFF, WS_SPG_ROWCNT, WS_SPG_TMP, WS_SPG_TABLE, WS_SPG_BIN,
+    WS_SPG_RESULT,
+    WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER,
+    WS_FILT_FLAGS, WS_FILT_SCAN,
+    WS_COUNT
+};
+
+// Per-kernel CUDA-event timing (enabled by pastis_ctx_profile).
+struct prof_rec {
+    const char *name;
+    cudaEvent_t ev0, ev1;
+};
+#define PASTIS_PROF_MAX 8192
+#define PASTIS_PROF_NAMES 64
+
+struct pastis_ctx {
+    int device;
+    cudaStream_t stream;
+    void *ws[WS_COUNT];
+    size_t ws_bytes[WS_COUNT];
+    int64_t launches;
+    int sm_count;
+    size_t smem_optin;
+    // kept result of the last overlap product (two-phase size protocol)
+    int64_t spg_n;
+    const void *spg_key_a;
+    int64_t spg_key_nnz;
+    int32_t spg_key_m, spg_key_min, spg_key_k;
+    uint32_t spg_key_mat_hash;
+    int spg_valid;
+    // kept result of the last filter
+    int64_t filt_n;
+    // profiling: pending event pairs and per-name totals
+    int prof_on;
+    int prof_open;
+    int prof_n;
+    prof_rec prof[PASTIS_PROF_MAX];
+    int prof_names;
+    const char *prof_name[PASTIS_PROF_NAMES];
+    int64_t prof_count[PASTIS_PROF_NAMES];
+    double prof_ms[PASTIS_PROF_NAMES];
+};
+
+// Records an event before (begin) and after (end) a kernel when profiling is on.
+void prof_begin(pastis_ctx *c, const char *name);
+void prof_end(pastis_ctx *c);
+
+// Grows workspace slot s to at least `bytes`; returns nullptr on failure.
+void *ws_get(pastis_ctx *c, int s, size_t bytes);
+
+#define PASTIS_CUDA_TRY(expr)                                   \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return PASTIS_ERR_CUDA;          \
+    } while (0)
+
+#define PASTIS_LAUNCHED(ctx)                                    \
+    do {                                                        \
+        (ctx)->launches++;                                      \
+        cudaError_t _e = cudaGetLastError();                    \
+        if (_e != cudaSuccess) return PASTIS_ERR_CUDA;          \
+    } while (0)
+
+#define PASTIS_WS(ptr, ctx, slot, bytes)                        \
+    do {                                                        \
+        (ptr) = (decltype(ptr))ws_get((ctx), (slot), (bytes));  \
+        if (!(ptr)) return PASTIS_ERR_OUT_OF_MEMORY;            \
+    } while (0)
+
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static inline int64_t ipow24(int k) {
+    int64_t v = 1;
+    for (int t = 0; t < k; ++t) v *= PASTIS_NSYM;
+    return v;
+}
+
+// Device radix sort (LSD, 8-bit digits, stable) of (uint32 key, uint64 value) pairs.
+// Sorts keys[0..n) by bits [0, key_bits); the result lands in *keys_out/*vals_out,
+// which point at either the input arrays or the two alternate arrays.
+pastis_status radix_sort_u32_u64(pastis_ctx *c, uint32_t *keys, uint64_t *vals,
+                                 uint32_t *keys_alt, uint64_t *vals_alt, int64_t n,
+                                 int key_bits, uint32_t **keys_out, uint64_t **vals_out);
+
+// Exclusive scan of n uint32 counts into uint32 offsets (n+1 entries, last = total).
+pastis_status exclusive_scan_u32(pastis_ctx *c, const uint32_t *in, uint32_t *out, int64_t n);
+// Exclusive scan of n int64 values into int64 offsets (n+1 entries).
+pastis_status exclusive_scan_i64(pastis_ctx *c, const int64_t *in, int64_t *out, int64_t n);
+
+// Validates the parameters shared by the calls; returns PASTIS_OK or INVALID_ARG.
+pastis_status check_params(const pastis_params *p);
+uint32_t params_matrix_hash(const pastis_params *p);

@@ -1,0 +1,264 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, bit-exact (all work is
+integer; the one float, the edge weight, is a correctly rounded quotient on both sides).
+Sizes span several tiles, stripes and ragged tails; edge cases cover empty and short
+sequences, repeats and the degenerate alignments."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+MAT = synth.blosum62()
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2009_14467_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def edge_case_set():
+    strings = ["", "A", "ACDEF", "ACDEFG", "AAAAAAAAAAAAAAAAAAAA", "WWWWWWW", "ACDEFGACDEFGACDEFG",
+               "MKV" * 40, "", "GGGGGGGGGGGGGGGGGGGGGGGGGGGGGGG", "ACDEFGHIKLMNPQRSTVWY" * 3]
+    rng = np.random.default_rng(7)
+    strings += [''.join(rng.choice(list(synth.ALPHABET[:20]), size=int(rng.integers(0, 300))))
+                for _ in range(40)]
+    return synth.from_strings(strings)
+
+
+# ---- a1 ------------------------------------------------------------------------------
+
+def test_encode_parity_and_errors(P, ctx):
+    ps = synth.families_1k()
+    got = P.encode(ctx, dev(ps.ascii)).cpu().numpy()
+    assert (got == O.encode(ps.ascii)).all()
+    # unaligned view and ragged tail
+    sub = dev(ps.ascii)[3:3 + 1001]
+    assert (P.encode(ctx, sub).cpu().numpy() == O.encode(ps.ascii[3:1004])).all()
+    bad = ps.ascii.copy()
+    bad[777] = ord("a")
+    bad[9000] = ord("J")
+    with pytest.raises(P.PastisError) as e:
+        P.encode(ctx, dev(bad))
+    assert e.value.status == 2 and "777" in str(e.value)
+
+
+# ---- a2-a3 ---------------------------------------------------------------------------
+
+def _oracle_csc(rp, code, pos, n, k):
+    seq = np.repeat(np.arange(n, dtype=np.int32), np.diff(rp))
+    order = np.lexsort((seq, code))
+    counts = np.bincount(code, minlength=24 ** k)
+    col_ptr = np.zeros(24 ** k + 1, np.int64)
+    np.cumsum(counts, out=col_ptr[1:])
+    return col_ptr, seq[order], pos[order]
+
+
+@pytest.mark.parametrize("which,k", [("families", 6), ("families", 3), ("edge", 6), ("edge", 2), ("edge", 1)])
+def test_build_kmers_parity(P, ctx, which, k):
+    ps = synth.families_1k() if which == "families" else edge_case_set()
+    codes = O.encode(ps.ascii)
+    rp, code, pos = O.kmers(codes, ps.offsets, k)
+    A = P.build_kmers(ctx, dev(codes), dev(ps.offsets), k)
+    assert A.nnz == code.size
+    assert (A.row_ptr.cpu().numpy() == rp).all()
+    assert (A.row_code[:A.nnz].cpu().numpy().view(np.uint32) == code).all()
+    assert (A.row_pos[:A.nnz].cpu().numpy().view(np.uint16) == pos).all()
+    cp, cs, cpos = _oracle_csc(rp, code, pos, ps.n, k)
+    assert (A.col_ptr.cpu().numpy().view(np.uint32).astype(np.int64) == cp).all()
+    assert (A.col_seq[:A.nnz].cpu().numpy() == cs).all()
+    assert (A.col_pos[:A.nnz].cpu().numpy().view(np.uint16) == cpos).all()
+
+
+# ---- a4 ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k,m", [(6, 25), (6, 50), (3, 25), (2, 40), (1, 23), (6, 128)])
+def test_substitute_kmers_parity(P, ctx, k, m):
+    rng = np.random.default_rng(k * 1000 + m)
+    roots = rng.choice(24 ** k, size=min(3000, 24 ** k), replace=False).astype(np.uint32)
+    # include roots made of the odd symbols (negative expenses for X, B/Z ties, *)
+    extra = [sum(c * 24 ** (k - 1 - t) for t, c in enumerate(w[:k]))
+             for w in ([22] * 6, [20, 21, 22, 23, 22, 20], [23] * 6, [4] * 6, [17] * 6)]
+    roots = np.unique(np.concatenate([roots, np.array(extra, np.uint32)]))
+    want_c, want_d = O.subkmers(roots, k, m, MAT)
+    gc, gd = P.substitute_kmers(ctx, dev(roots.view(np.int32)), P.Params(matrix=MAT, k=k, m_subs=m))
+    assert (gc.cpu().numpy().view(np.uint32) == want_c).all()
+    assert (gd.cpu().numpy() == want_d).all()
+
+
+# ---- a5-a7 ---------------------------------------------------------------------------
+
+def _cands(P, ctx, ps, k=6, m=0, min_shared=1):
+    codes = O.encode(ps.ascii)
+    A = P.build_kmers(ctx, dev(codes), dev(ps.offsets), k)
+    got = P.to_records(P.overlap_spgemm(ctx, A, P.Params(matrix=MAT, k=k, m_subs=m, min_shared=min_shared)),
+                       P.CAND_DTYPE)
+    rp, code, pos = O.kmers(codes, ps.offsets, k)
+    want = O.candidates(rp, code, pos, k, m, MAT, min_shared)
+    return got, want
+
+
+@pytest.mark.parametrize("min_shared", [1, 2, 4])
+def test_candidates_exact_parity(P, ctx, min_shared):
+    got, want = _cands(P, ctx, synth.families_1k(), min_shared=min_shared)
+    assert len(got) == len(want)
+    assert got.tobytes() == want.tobytes()
+
+
+def test_candidates_exact_edge_cases(P, ctx):
+    ps = edge_case_set()
+    for k in (1, 2, 6):
+        got, want = _cands(P, ctx, ps, k=k)
+        assert got.tobytes() == want.tobytes()
+
+
+def test_candidates_split_rows(P, ctx):
+    # many copies of one family: rows exceed a shared-memory table and are split
+    fam = synth.planted_families([700], 0, (60, 120), seed=11)
+    got, want = _cands(P, ctx, fam, k=3)
+    assert got.tobytes() == want.tobytes()
+
+
+@pytest.mark.parametrize("m,min_shared,k", [(25, 1, 6), (10, 4, 6), (5, 1, 4)])
+def test_candidates_substitute_parity(P, ctx, m, min_shared, k):
+    ps = synth.zipf_100k(n=2000).subset(np.arange(300))
+    got, want = _cands(P, ctx, ps, k=k, m=m, min_shared=min_shared)
+    assert len(got) == len(want)
+    assert got.tobytes() == want.tobytes()
+
+
+def test_spgemm_capacity_protocol(P, ctx):
+    ps = synth.families_1k().subset(np.arange(200))
+    codes = O.encode(ps.ascii)
+    A = P.build_kmers(ctx, dev(codes), dev(ps.offsets), 6)
+    p = P.Params(matrix=MAT).c()
+    nout = ctypes.c_int64()
+    st = P.pastis.lib().pastis_overlap_spgemm(ctx.h, ctypes.byref(A.c()), ctypes.byref(p), None, 0,
+                                                ctypes.byref(nout))
+    assert st == 3 and nout.value > 0
+    out = torch.empty((nout.value, 20), dtype=torch.uint8, device="cuda")
+    st = P.pastis.lib().pastis_overlap_spgemm(ctx.h, ctypes.byref(A.c()), ctypes.byref(p),
+                                                ctypes.c_void_p(out.data_ptr()), nout.value, ctypes.byref(nout))
+    assert st == 0
+
+
+# ---- a8-a10 --------------------------------------------------------------------------
+
+def _align_both(P, ctx, ps, cands, mode, **kw):
+    codes = O.encode(ps.ascii)
+    params = P.Params(matrix=MAT, mode=mode, **kw)
+    cells = torch.zeros(1, dtype=torch.int64, device="cuda")
+    got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets), dev(cands.view(np.uint8).reshape(-1, 20)),
+                                     params, cells), P.ALN_DTYPE)
+    want, wcells = O.align_pairs(codes, ps.offsets, cands, MAT, params.gap_open, params.gap_extend, mode,
+                                 params.xdrop, params.k, params.ani_min_pct, params.cov_min_pct)
+    return got, want, int(cells.item()), wcells
+
+
+def _cmp_alns(got, want):
+    for f in ("score", "qb", "qe", "tb", "te", "ident", "cols", "seed_used", "passes"):
+        bad = np.flatnonzero(got[f] != want[f])
+        assert bad.size == 0, f"{f} differs at {bad[:5]}: {got[bad[:3]]} vs {want[bad[:3]]}"
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_align_parity_families(P, ctx, mode):
+    ps = synth.families_1k()
+    _, cands = _cands(P, ctx, ps)
+    got, want, cells, wcells = _align_both(P, ctx, ps, cands, mode)
+    _cmp_alns(got, want)
+    assert cells == wcells
+
+
+def _all_pairs(n):
+    i, j = np.triu_indices(n, 1)
+    c = np.zeros(i.size, O.CAND_DTYPE)
+    c['i'], c['j'], c['count'] = i, j, 1
+    return c
+
+
+@pytest.mark.parametrize("o,e", [(11, 1), (3, 1), (1, 1)])
+def test_sw_parity_edge_cases(P, ctx, o, e):
+    ps = edge_case_set()
+    cands = _all_pairs(ps.n)
+    got, want, cells, wcells = _align_both(P, ctx, ps, cands, 0, gap_open=o, gap_extend=e)
+    _cmp_alns(got, want)
+    assert cells == wcells
+
+
+def test_sw_parity_long_and_lopsided(P, ctx):
+    rng = np.random.default_rng(3)
+    fam = synth.planted_families([4, 3], 2, (1500, 2000), seed=5)
+    short = synth.from_strings([''.join(rng.choice(list(synth.ALPHABET[:20]), size=L)) for L in (1, 31, 33, 257, 513)])
+    strings = [fam.seq(i) for i in range(fam.n)] + [short.seq(i) for i in range(short.n)]
+    ps = synth.from_strings(strings)
+    cands = _all_pairs(ps.n)
+    got, want, _, _ = _align_both(P, ctx, ps, cands, 0)
+    _cmp_alns(got, want)
+
+
+@pytest.mark.parametrize("X", [49, 5, 0, 1000])
+def test_xd_parity_x_values(P, ctx, X):
+    ps = synth.families_1k().subset(np.arange(300))
+    _, cands = _cands(P, ctx, ps)
+    got, want, cells, wcells = _align_both(P, ctx, ps, cands, 1, xdrop=X)
+    _cmp_alns(got, want)
+    assert cells == wcells
+
+
+def test_xd_parity_substitute_seeds(P, ctx):
+    ps = synth.zipf_100k(n=2000).subset(np.arange(200))
+    _, cands = _cands(P, ctx, ps, m=25)
+    got, want, cells, wcells = _align_both(P, ctx, ps, cands, 1)
+    _cmp_alns(got, want)
+    assert cells == wcells
+
+
+def test_align_rejects_bad_pairs(P, ctx):
+    ps = synth.families_1k().subset(np.arange(10))
+    cands = _all_pairs(ps.n)
+    cands['j'][3] = 10
+    with pytest.raises(P.PastisError) as e:
+        _align_both(P, ctx, ps, cands, 0)
+    assert e.value.status == 1
+
+
+def test_filter_and_end_to_end(P, ctx):
+    ps = synth.families_1k()
+    params = P.Params(matrix=MAT)
+    res = P.run(ctx, dev(ps.ascii), dev(ps.offsets), params)
+    ref = O.run(ps.ascii, ps.offsets, MAT)
+    assert P.to_records(res["cands"], P.CAND_DTYPE).tobytes() == ref["cands"].tobytes()
+    _cmp_alns(P.to_records(res["alns"], P.ALN_DTYPE), ref["alns"])
+    assert P.to_records(res["edges"], P.EDGE_DTYPE).tobytes() == ref["edges"].tobytes()
+
+
+def test_profiler_counts_kernels(P, ctx):
+    ps = synth.families_1k().subset(np.arange(200))
+    params = P.Params(matrix=MAT)
+    for _ in range(2):
+        ctx.profile(True)
+        P.run(ctx, dev(ps.ascii), dev(ps.offsets), params)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_items", "sw_pass1", "sw_pass2",
+                     "filter_flags"):
+            assert name in prof and prof[name][0] >= 1 and prof[name][1] >= 0.0, name
