@@ -42,6 +42,7 @@ WORKLOADS = {
         "k=6 with 25 substitute k-mers (C = A S A^T, symmetrized), min_shared 1, "
         "SW int32 BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
     "zipf_20k_s25_sw": dict(n=20_000, m=25, mode=0, desc="20,000 proteins, same recipe (smaller stand-in)"),
+    "zipf_5k_s25_sw": dict(n=5_000, m=25, mode=0, desc="5,000 proteins, same recipe (profiling stand-in)"),
     "families_1k_sw": dict(n=1000, m=0, mode=0, desc=(
         "1,000 proteins = 100 families x 10, k=6 exact, SW int32, ANI 30 / cov 70")),
 }

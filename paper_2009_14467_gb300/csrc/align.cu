@@ -1,268 +1,33 @@
-// a8-a9: Smith-Waterman and x-drop alignment of candidate pairs (Sec. IV-E, Sec. VI).
-//
-// Smith-Waterman, affine gaps (a gap of length L costs open + (L-1)*extend):
-//   E(i,j) = max(H(i,j-1) - o, E(i,j-1) - e)     F(i,j) = max(H(i-1,j) - o, F(i-1,j) - e)
-//   H(i,j) = max(0, H(i-1,j-1) + s(q_i, t_j), F(i,j), E(i,j))
-// The reported alignment is the one a traceback from the end cell (the first maximum
-// in row-major order) selects when it prefers the diagonal, then F, then E, and a gap
-// open over an extension.  The GPU never traces back: every state carries, along the
-// predecessor that traceback would take, the statistic it needs, so the value held at
-// the end cell is the traceback's.
-//
-// Two passes over a warp wavefront:
-//   pass 1 (whole matrix) carries the alignment's begin cell; it gives score, end and
-//          begin, hence both spans, for every pair;
-//   pass 2 (only the rectangle [qb, qe) x [tb, te)) carries identities and matched
-//          columns.  Inside that rectangle, with zero boundaries, every cell of the
-//          traced path keeps its value and every choice along it stays the same, so
-//          the carried statistic at the end cell is the full matrix's.  Random pairs
-//          have short alignments, so pass 2 costs little.
-// Wavefront: lane l of a warp owns R consecutive query rows; at step s it computes
-// column j = s - l for its rows, taking the bottom H/F (and carries) of lane l-1's
-// previous step through __shfl_up_sync.  Queries longer than 32R rows are done in
-// stripes; the last row of a stripe goes to the next through a per-warp buffer.
+// a8-a9: the alignment entry point and the x-drop seed-and-extend (Sec. IV-E, Sec. VI).
+// Smith-Waterman lives in sw.cu.
 //
 // x-drop (XD): from a seed, the seed's score plus two anchored extensions (right of
 // the seed, and left of it on the reversed prefixes), each computed antidiagonal by
 // antidiagonal by one warp: cells of antidiagonal d+1 are those adjacent to the live
 // range of d, a cell dies when H < best - X (best over the earlier antidiagonals),
-// and the extension ends when an antidiagonal has no live cell.
+// and the extension ends when an antidiagonal has no live cell.  Every state carries
+// (identities << 16 | matched columns) along the predecessor a traceback would take
+// (diagonal > F > E, open > extend), so the end cell holds the path's statistics.
 #include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
+
+pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets, const pastis_cand *d_pairs,
+                       int64_t n_pairs, const pastis_params *p, const int8_t *dmat, int *flags, int lmax,
+                       pastis_aln *d_out, int64_t *d_cells);
 
 namespace {
 
 constexpr int NEG = -1000000000;
 constexpr int ALN_THREADS = 256;
 constexpr int ALN_WARPS = ALN_THREADS / 32;
-constexpr int SW_R = 8;                  // query rows per lane
-constexpr int STRIPE = 32 * SW_R;
-constexpr int PAD_CODE = PASTIS_NSYM;    // score row for rows past the end of the query
 constexpr int PAD_SCORE = -30000;
-
-struct sw_pass1_out {                     // per pair
-    int32_t score;
-    uint32_t end;                         // (row << 16) | col
-    uint32_t begin;                       // (row << 16) | col
-    int32_t pad;
-};
-
-__device__ __forceinline__ uint32_t pack_rc(int r, int c) { return ((uint32_t)r << 16) | (uint32_t)c; }
-
-// Scratch row handed between stripes: H, F and their carries for every column.
-struct stripe_cell { int32_t h, f; uint32_t hc, fc; };
-
-// One warp computes one matrix.  MODE 1: carry = begin cell; tracks the first maximum.
-// MODE 2: carry = ident << 16 | matched columns; reports the carry at (m-1, n-1).
-template <int MODE>
-__device__ void sw_warp(const uint8_t *__restrict__ q, int m, const uint8_t *__restrict__ t, int n,
-                        const int *__restrict__ s_mat, int o, int e, stripe_cell *scratch, int sstride,
-                        int *best_out,
-                        int *best_row_out, int *best_col_out, uint32_t *best_carry_out) {
-    const int lane = threadIdx.x & 31;
-    int best = 0, best_row = 0x7FFFFFFF, best_col = 0;
-    uint32_t best_carry = 0;
-    int end_h = NEG;
-    uint32_t end_c = 0;
-    const int nstripes = (m + STRIPE - 1) / STRIPE;
-    for (int stripe = 0; stripe < nstripes; ++stripe) {
-        const int row0 = stripe * STRIPE + lane * SW_R;
-        int qoff[SW_R];
-        int Hc[SW_R], Ec[SW_R];
-        uint32_t HCc[SW_R], ECc[SW_R];
-#pragma unroll
-        for (int r = 0; r < SW_R; ++r) {
-            const int i = row0 + r;
-            qoff[r] = (i < m ? (int)q[i] : PAD_CODE) * 32;
-            Hc[r] = 0;
-            Ec[r] = NEG;
-            HCc[r] = MODE == 1 ? pack_rc(i + 1, 0) : 0u;
-            ECc[r] = 0;
-        }
-        int dtop_h = 0;                                   // H(row0-1, j-1)
-        uint32_t dtop_c = MODE == 1 ? pack_rc(row0, 0) : 0u;
-        int out_h = 0, out_f = NEG, out_t = 0;
-        uint32_t out_hc = 0, out_fc = 0;
-        const stripe_cell *in_buf = scratch + (size_t)(stripe & 1) * sstride;
-        stripe_cell *out_buf = scratch + (size_t)((stripe + 1) & 1) * sstride;
-        const bool last_stripe = stripe + 1 == nstripes;
-        const int nsteps = n + 31;
-        for (int s = 0; s < nsteps; ++s) {
-            const int j = s - lane;
-            int up_h = __shfl_up_sync(0xffffffffu, out_h, 1);
-            int up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
-            uint32_t up_hc = __shfl_up_sync(0xffffffffu, out_hc, 1);
-            uint32_t up_fc = __shfl_up_sync(0xffffffffu, out_fc, 1);
-            int tj = __shfl_up_sync(0xffffffffu, out_t, 1);
-            if (lane == 0 && j < n) {
-                tj = t[j];
-                if (stripe == 0) {
-                    up_h = 0; up_f = NEG;
-                    up_hc = MODE == 1 ? pack_rc(0, j + 1) : 0u;
-                    up_fc = 0;
-                } else {
-                    stripe_cell c = in_buf[j];
-                    up_h = c.h; up_f = c.f; up_hc = c.hc; up_fc = c.fc;
-                }
-            }
-            if (j >= 0 && j < n) {
-                int dh = dtop_h;
-                uint32_t dc = dtop_c;
-                int ah = up_h;
-                uint32_t ac = up_hc;
-                int f = up_f;
-                uint32_t fc = up_fc;
-#pragma unroll
-                for (int r = 0; r < SW_R; ++r) {
-                    const int i = row0 + r;
-                    // E: horizontal gap, from (i, j-1)
-                    const int eo = Hc[r] - o, ex = Ec[r] - e;
-                    const bool eopen = eo >= ex;
-                    const int ev = eopen ? eo : ex;
-                    const uint32_t evc = eopen ? HCc[r] : ECc[r];
-                    // F: vertical gap, from (i-1, j)
-                    const int fo = ah - o, fx = f - e;
-                    const bool fopen = fo >= fx;
-                    f = fopen ? fo : fx;
-                    fc = fopen ? ac : fc;
-                    // H: diagonal > F > E, restart at 0
-                    const int sc = s_mat[qoff[r] + tj];
-                    int h = dh + sc;
-                    uint32_t hc;
-                    if (MODE == 1) hc = dc;
-                    else hc = dc + ((qoff[r] == tj * 32) ? 0x10001u : 1u);
-                    if (f > h) { h = f; hc = fc; }
-                    if (ev > h) { h = ev; hc = evc; }
-                    if (h <= 0) { h = 0; hc = MODE == 1 ? pack_rc(i + 1, j + 1) : 0u; }
-                    if (MODE == 1) {
-                        if (i < m && (h > best || (h == best && h > 0 && i < best_row))) {
-                            best = h; best_row = i; best_col = j; best_carry = hc;
-                        }
-                    } else {
-                        if (i == m - 1 && j == n - 1) { end_h = h; end_c = hc; }
-                    }
-                    dh = Hc[r];
-                    dc = HCc[r];
-                    Hc[r] = h; HCc[r] = hc;
-                    Ec[r] = ev; ECc[r] = evc;
-                    ah = h; ac = hc;
-                }
-                dtop_h = up_h;
-                dtop_c = up_hc;
-                out_h = ah; out_hc = ac; out_f = f; out_fc = fc; out_t = tj;
-                if (lane == 31 && !last_stripe) out_buf[j] = stripe_cell{ah, f, ac, fc};
-            }
-        }
-        __syncwarp();
-    }
-    if (MODE == 1) {
-        // first maximum in row-major order across the warp
-        for (int d = 16; d > 0; d >>= 1) {
-            int ob = __shfl_xor_sync(0xffffffffu, best, d);
-            int orow = __shfl_xor_sync(0xffffffffu, best_row, d);
-            int ocol = __shfl_xor_sync(0xffffffffu, best_col, d);
-            uint32_t oc = __shfl_xor_sync(0xffffffffu, best_carry, d);
-            bool take = ob > best || (ob == best && (orow < best_row || (orow == best_row && ocol < best_col)));
-            if (take) { best = ob; best_row = orow; best_col = ocol; best_carry = oc; }
-        }
-        *best_out = best; *best_row_out = best_row; *best_col_out = best_col; *best_carry_out = best_carry;
-    } else {
-        for (int d = 16; d > 0; d >>= 1) {
-            int oh = __shfl_xor_sync(0xffffffffu, end_h, d);
-            uint32_t oc = __shfl_xor_sync(0xffffffffu, end_c, d);
-            if (oh > end_h) { end_h = oh; end_c = oc; }
-        }
-        *best_out = end_h; *best_carry_out = end_c;
-    }
-}
 
 __device__ void load_matrix(const int8_t *gmat, int *s_mat) {
     for (int x = threadIdx.x; x < (PASTIS_NSYM + 1) * 32; x += blockDim.x) {
         int a = x / 32, b = x % 32;
         s_mat[x] = (a < PASTIS_NSYM && b < PASTIS_NSYM) ? (int)gmat[a * PASTIS_NSYM + b] : PAD_SCORE;
-    }
-}
-
-__global__ void __launch_bounds__(ALN_THREADS) k_sw_pass1(const uint8_t *codes, const int64_t *offsets,
-                                                          const pastis_cand *pairs, int64_t n_pairs,
-                                                          const int8_t *gmat, int o, int e,
-                                                          stripe_cell *scratch, int sstride, int *next_pair,
-                                                          sw_pass1_out *out, unsigned long long *cells) {
-    __shared__ int s_mat[(PASTIS_NSYM + 1) * 32];
-    load_matrix(gmat, s_mat);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * ALN_WARPS + (threadIdx.x >> 5);
-    stripe_cell *my = scratch + (size_t)gw * 2 * sstride;
-    unsigned long long my_cells = 0;
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(next_pair, 1);
-        p = __shfl_sync(0xffffffffu, p, 0);
-        if (p >= n_pairs) break;
-        const pastis_cand c = pairs[p];
-        const int64_t qo = offsets[c.i], to = offsets[c.j];
-        const int m = (int)(offsets[c.i + 1] - qo), n = (int)(offsets[c.j + 1] - to);
-        int best = 0, brow = 0, bcol = 0;
-        uint32_t bc = 0;
-        if (m > 0 && n > 0)
-            sw_warp<1>(codes + qo, m, codes + to, n, s_mat, o, e, my, sstride, &best, &brow, &bcol, &bc);
-        if (lane == 0) {
-            sw_pass1_out r;
-            r.score = best;
-            r.end = best > 0 ? pack_rc(brow, bcol) : 0u;
-            r.begin = best > 0 ? bc : 0u;
-            r.pad = 0;
-            out[p] = r;
-            my_cells += (unsigned long long)m * (unsigned long long)n;
-        }
-    }
-    if (lane == 0 && cells) atomicAdd(cells, my_cells);
-}
-
-__global__ void __launch_bounds__(ALN_THREADS) k_sw_pass2(const uint8_t *codes, const int64_t *offsets,
-                                                          const pastis_cand *pairs, int64_t n_pairs,
-                                                          const int8_t *gmat, int o, int e, int ani, int cov,
-                                                          stripe_cell *scratch, int sstride, int *next_pair,
-                                                          const sw_pass1_out *p1, pastis_aln *out, int *err) {
-    __shared__ int s_mat[(PASTIS_NSYM + 1) * 32];
-    load_matrix(gmat, s_mat);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * ALN_WARPS + (threadIdx.x >> 5);
-    stripe_cell *my = scratch + (size_t)gw * 2 * sstride;
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(next_pair, 1);
-        p = __shfl_sync(0xffffffffu, p, 0);
-        if (p >= n_pairs) break;
-        const pastis_cand c = pairs[p];
-        const sw_pass1_out r1 = p1[p];
-        pastis_aln rec;
-        rec.score = 0; rec.qb = rec.qe = rec.tb = rec.te = 0; rec.ident = rec.cols = 0;
-        rec.seed_used = 0; rec.passes = 0; rec.reserved = 0;
-        if (r1.score > 0) {
-            const int64_t qo = offsets[c.i], to = offsets[c.j];
-            const int lq = (int)(offsets[c.i + 1] - qo), lt = (int)(offsets[c.j + 1] - to);
-            const int qb = (int)(r1.begin >> 16), tb = (int)(r1.begin & 0xFFFF);
-            const int qe = (int)(r1.end >> 16) + 1, te = (int)(r1.end & 0xFFFF) + 1;
-            int endh = 0, dummy_r = 0, dummy_c = 0;
-            uint32_t carry = 0;
-            sw_warp<2>(codes + qo + qb, qe - qb, codes + to + tb, te - tb, s_mat, o, e, my, sstride, &endh, &dummy_r,
-                       &dummy_c, &carry);
-            const int M = (int)(carry & 0xFFFF), ident = (int)(carry >> 16);
-            rec.score = r1.score;
-            rec.qb = (uint16_t)qb; rec.qe = (uint16_t)qe; rec.tb = (uint16_t)tb; rec.te = (uint16_t)te;
-            rec.ident = (uint16_t)ident;
-            rec.cols = (uint16_t)((qe - qb) + (te - tb) - M);
-            if (endh != r1.score && lane == 0) atomicExch(err, 1);
-            const int span = lq <= lt ? qe - qb : te - tb;
-            const int L = lq <= lt ? lq : lt;
-            rec.passes = (rec.cols > 0 && 100 * (int)rec.ident >= ani * (int)rec.cols && 100 * span >= cov * L) ? 1 : 0;
-        }
-        if (lane == 0) out[p] = rec;
     }
 }
 
@@ -525,23 +290,8 @@ extern "C" pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_co
     const int blocks = ctx->sm_count * 2;
     const int nwarps = blocks * ALN_WARPS;
     if (!xd) {
-        const int sstride = lmax + 1;
-        stripe_cell *scratch;
-        PASTIS_WS(scratch, ctx, WS_ALN_SCRATCH, sizeof(stripe_cell) * (size_t)nwarps * 2 * sstride);
-        sw_pass1_out *p1;
-        PASTIS_WS(p1, ctx, WS_ALN_PASS1, sizeof(sw_pass1_out) * (size_t)n_pairs);
-        prof_begin(ctx, "sw_pass1");
-        k_sw_pass1<<<blocks, ALN_THREADS, 0, st>>>(d_codes, d_offsets, d_pairs, n_pairs, dmat, params->gap_open,
-                                                   params->gap_extend, scratch, sstride, flags + 1, p1,
-                                                   (unsigned long long *)d_cells);
-        PASTIS_LAUNCHED(ctx);
-        prof_end(ctx);
-        prof_begin(ctx, "sw_pass2");
-        k_sw_pass2<<<blocks, ALN_THREADS, 0, st>>>(d_codes, d_offsets, d_pairs, n_pairs, dmat, params->gap_open,
-                                                   params->gap_extend, params->ani_min_pct, params->cov_min_pct,
-                                                   scratch, sstride, flags + 3, p1, d_out, flags);
-        PASTIS_LAUNCHED(ctx);
-        prof_end(ctx);
+        s = sw_align(ctx, d_codes, d_offsets, d_pairs, n_pairs, params, dmat, flags, lmax, d_out, d_cells);
+        if (s != PASTIS_OK) return s;
     } else {
         const int W = lmax + 2;
         int32_t *gbuf;

@@ -259,6 +259,6 @@ def test_profiler_counts_kernels(P, ctx):
         P.run(ctx, dev(ps.ascii), dev(ps.offsets), params)
         prof = ctx.profile_read()
         ctx.profile(False)
-        for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_items", "sw_pass1", "sw_pass2",
+        for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_items", "sw_pass1", "sw_pass3",
                      "filter_flags"):
             assert name in prof and prof[name][0] >= 1 and prof[name][1] >= 0.0, name
