@@ -198,6 +198,15 @@ pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kmat *A,
                                     const pastis_params *params, pastis_cand *d_out,
                                     int64_t capacity, int64_t *n_out);
 
+/* The rows row_begin <= i < row_end of the same product (every j > i): a block of
+ * queries against the whole set, for batched or partial formation of B (the paper's
+ * Sec. VII names partial formation of the output as the way to cap memory).  The
+ * result equals the matching slice of pastis_overlap_spgemm's.  Synchronises.        */
+pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pastis_kmat *A,
+                                         const pastis_params *params, int32_t row_begin,
+                                         int32_t row_end, pastis_cand *d_out, int64_t capacity,
+                                         int64_t *n_out);
+
 /* ---- a8-a9: alignment (Sec. IV-E) ---------------------------------------------- */
 
 /* One record per candidate, d_out[n_pairs].

@@ -44,7 +44,7 @@ struct pastis_ctx {
     int64_t spg_n;
     const void *spg_key_a;
     int64_t spg_key_nnz;
-    int32_t spg_key_m, spg_key_min, spg_key_k;
+    int32_t spg_key_m, spg_key_min, spg_key_k, spg_key_r0, spg_key_r1;
     uint32_t spg_key_mat_hash;
     int spg_valid;
     // kept result of the last filter

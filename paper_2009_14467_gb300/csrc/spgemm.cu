@@ -238,9 +238,11 @@ size_t table_bytes(int tsize, bool subs) {
 
 }  // namespace
 
-extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *params,
-                                               pastis_cand *d_out, int64_t capacity, int64_t *n_out) {
+extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pastis_kmat *A,
+                                                    const pastis_params *params, int32_t row_begin, int32_t row_end,
+                                                    pastis_cand *d_out, int64_t capacity, int64_t *n_out) {
     if (!ctx || !A || !n_out || capacity < 0) return PASTIS_ERR_INVALID_ARG;
+    if (row_begin < 0 || row_end < row_begin || row_end > A->n_rows) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
     if (A->k != params->k || A->n_rows < 0) return PASTIS_ERR_INVALID_ARG;
@@ -252,7 +254,8 @@ extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kma
     // a kept result for the same inputs: copy it (two-phase size protocol)
     if (ctx->spg_valid && ctx->spg_key_a == (const void *)A->row_ptr && ctx->spg_key_nnz == A->nnz &&
         ctx->spg_key_m == params->m_subs && ctx->spg_key_min == params->min_shared &&
-        ctx->spg_key_k == params->k && ctx->spg_key_mat_hash == (subs ? mh : 0u)) {
+        ctx->spg_key_k == params->k && ctx->spg_key_mat_hash == (subs ? mh : 0u) &&
+        ctx->spg_key_r0 == row_begin && ctx->spg_key_r1 == row_end) {
         *n_out = ctx->spg_n;
         if (capacity < ctx->spg_n) return PASTIS_ERR_CAPACITY;
         if (ctx->spg_n > 0) {
@@ -309,7 +312,7 @@ extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kma
     struct plan_item { int32_t i, j0, j1; int tlog; int64_t cap; };
     std::vector<plan_item> plan;
     plan.reserve((size_t)n);
-    for (int32_t i = 0; i + 1 < n; ++i) {
+    for (int32_t i = row_begin; i < row_end && i + 1 < n; ++i) {
         int64_t b = hb[i] + (subs ? hb[(size_t)n + i] : 0);
         int64_t width = n - 1 - i;
         int64_t est = std::min(b, width);
@@ -332,7 +335,7 @@ extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kma
 
     // upper bound of the records: distinct j per row
     int64_t ubound = 0;
-    for (int32_t i = 0; i + 1 < n; ++i)
+    for (int32_t i = row_begin; i < row_end && i + 1 < n; ++i)
         ubound += std::min<int64_t>(hb[i] + (subs ? hb[(size_t)n + i] : 0), (int64_t)(n - 1 - i));
     pastis_cand *result;
     PASTIS_WS(result, ctx, WS_SPG_RESULT, sizeof(pastis_cand) * (size_t)(ubound + 1));
@@ -496,6 +499,8 @@ extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kma
     ctx->spg_key_min = params->min_shared;
     ctx->spg_key_k = params->k;
     ctx->spg_key_mat_hash = subs ? mh : 0u;
+    ctx->spg_key_r0 = row_begin;
+    ctx->spg_key_r1 = row_end;
     *n_out = total;
     if (capacity < total) return PASTIS_ERR_CAPACITY;
     if (total > 0) {
@@ -504,4 +509,10 @@ extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kma
         PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *params,
+                                               pastis_cand *d_out, int64_t capacity, int64_t *n_out) {
+    if (!A) return PASTIS_ERR_INVALID_ARG;
+    return pastis_overlap_spgemm_rows(ctx, A, params, 0, A->n_rows, d_out, capacity, n_out);
 }

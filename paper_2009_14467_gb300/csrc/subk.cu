@@ -187,9 +187,16 @@ __global__ void k_compact_as(const uint32_t *keys, const uint64_t *vals, const u
     rvals[o] = ((uint64_t)keys[x] << 16) | pos;
 }
 
-__global__ void k_row_count_u32(const uint32_t *rkeys, int64_t nnz, int64_t *row_count) {
-    int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < nnz) atomicAdd((unsigned long long *)&row_count[rkeys[x]], 1ull);
+// row_ptr[r] = first index x with keys[x] >= r (keys sorted ascending), r = 0..n
+__global__ void k_row_count_u32(const uint32_t *keys, int64_t nnz, int32_t n, int64_t *row_ptr) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > n) return;
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)keys[mid] < r) lo = mid + 1; else hi = mid;
+    }
+    row_ptr[r] = lo;
 }
 
 __global__ void k_split_rows_as(const uint64_t *rvals, int64_t nnz, uint32_t *row_code, uint16_t *row_pos) {
@@ -335,16 +342,13 @@ pastis_status build_as(pastis_ctx *ctx, const pastis_kmat *A, const pastis_param
     uint64_t *rvo;
     s = radix_sort_u32_u64(ctx, rk, rv, sk, sv, nnz, bits_for_u64((uint64_t)(n > 0 ? n - 1 : 0)), &rko, &rvo);
     if (s != PASTIS_OK) return s;
-    int64_t *row_count;
-    PASTIS_WS(row_count, ctx, WS_SPG_ROWCNT, sizeof(int64_t) * (n + 1));
-    PASTIS_CUDA_TRY(cudaMemsetAsync(row_count, 0, sizeof(int64_t) * (n + 1), st));
+    prof_begin(ctx, "as_rowptr");
+    k_row_count_u32<<<(unsigned)ceil_div64((int64_t)n + 1, 256), 256, 0, st>>>(rko, nnz, n, out->row_ptr);
+    PASTIS_LAUNCHED(ctx);
+    prof_end(ctx);
     if (nnz > 0) {
-        k_row_count_u32<<<(unsigned)ceil_div64(nnz, 256), 256, 0, st>>>(rko, nnz, row_count);
-        PASTIS_LAUNCHED(ctx);
         k_split_rows_as<<<(unsigned)ceil_div64(nnz, 256), 256, 0, st>>>(rvo, nnz, out->row_code, out->row_pos);
         PASTIS_LAUNCHED(ctx);
     }
-    s = exclusive_scan_i64(ctx, row_count, out->row_ptr, n);
-    if (s != PASTIS_OK) return s;
     return PASTIS_OK;
 }

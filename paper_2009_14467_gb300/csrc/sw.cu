@@ -79,7 +79,7 @@ __device__ __forceinline__ int sx_hi(uint32_t w) { return (int)w >> 16; }
 // rows, the largest H of the lane block that holds it (an upper bound per row).
 template <int LR>
 __device__ void score_warp(const int16_t *__restrict__ prof, int prow, const uint8_t *__restrict__ t, int m,
-                           int n, int o, int e, stripe1_cell *scratch, int sstride, int *bm4, int *best_h,
+                           int n, int o, int e, stripe1_cell *scratch, int sstride, int16_t *bm4, int *best_h,
                            int *best_i, int *best_j) {
     constexpr int STRIPE = 32 * LR;
     const int lane = threadIdx.x & 31;
@@ -159,7 +159,7 @@ __device__ void score_warp(const int16_t *__restrict__ prof, int prow, const uin
             }
         }
 #pragma unroll
-        for (int g = 0; g < LR / 2; ++g) bm4[(row0 >> 1) + g] = blockkey >> 16;
+        for (int g = 0; g < LR / 2; ++g) bm4[(row0 >> 1) + g] = (int16_t)(blockkey >> 16);
         __syncwarp();
     }
     // row-major first maximum across the warp: the largest key (ties cannot cross lanes)
@@ -188,7 +188,7 @@ constexpr int WIN = 64;           // cells of one antidiagonal kept in shared me
 // window of WIN cells per array; a live band wider than that returns false and the
 // caller falls back to the whole up-left rectangle.
 __device__ bool bound_warp(const uint8_t *q, int A, const uint8_t *t, int B, const int8_t *s_mat8, int o, int e,
-                           int S, int ei, const int *bm4, int32_t *win, int *amax_out, int *bmax_out) {
+                           int S, int ei, const int16_t *bm4, int32_t *win, int *amax_out, int *bmax_out) {
     // q[-a], t[-b] for a, b >= 0 walk backwards from the end cell (ei, ej).  The cells of
     // antidiagonal d are those next to the live cells of d-1 (up, left) or of d-2
     // (diagonal).
@@ -230,7 +230,7 @@ __device__ bool bound_warp(const uint8_t *q, int A, const uint8_t *t, int B, con
                 if (fv < NEG) fv = NEG;
                 int h = max(max(dv, fv), ev);
                 const int i = ei - a + 1;                 // first forward row of the suffix
-                const int thr = S - (i >= 1 ? bm4[(i - 1) >> 1] : 0) - slack;
+                const int thr = S - (i >= 1 ? (int)bm4[(i - 1) >> 1] : 0) - slack;
                 if (h < thr) { h = NEG; ev = NEG; fv = NEG; }
                 Hd[x] = h; Ed[x] = ev; Fd[x] = fv;
                 if (h != NEG) {
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *codes
                                                          int max_s, int prow_cap, char *scratch, size_t warp_bytes,
                                                          int sstride, int *next_seg, sw_score_out *out,
                                                          unsigned long long *cells) {
-    // dynamic shared memory: profile [24][prow_cap] int16, then per warp bm4[prow_cap/2]
+    // dynamic shared memory: profile [24][prow_cap] int16, then per warp bm4[prow_cap/2] int16
     // and the pass-2 window [9][WIN]
     extern __shared__ __align__(16) int16_t s_prof[];
     __shared__ int s_seg, s_next;
@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *codes
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * SW_WARPS + warp;
     for (int x = threadIdx.x; x < PASTIS_NSYM * PASTIS_NSYM; x += blockDim.x) s_mat8[x] = gmat[x];
-    int *bm4 = reinterpret_cast<int *>(s_prof + PASTIS_NSYM * prow_cap) + warp * (prow_cap / 2);
-    int32_t *win = reinterpret_cast<int32_t *>(s_prof + PASTIS_NSYM * prow_cap) + SW_WARPS * (prow_cap / 2) +
+    int16_t *bm4 = s_prof + PASTIS_NSYM * prow_cap + warp * (prow_cap / 2);
+    int32_t *win = reinterpret_cast<int32_t *>(s_prof + PASTIS_NSYM * prow_cap + SW_WARPS * (prow_cap / 2)) +
                    warp * 9 * WIN;
     stripe1_cell *my = reinterpret_cast<stripe1_cell *>(scratch + (size_t)gw * warp_bytes);
     unsigned long long my_cells = 0;
@@ -682,7 +682,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d
     int prow_cap = ((lmax + STRIPE1 - 1) / STRIPE1) * STRIPE1;
     if (prow_cap < STRIPE1) prow_cap = STRIPE1;
     auto shm_for = [](int pc) {
-        return (size_t)PASTIS_NSYM * pc * 2 + (size_t)SW_WARPS * (pc / 2) * 4 + (size_t)SW_WARPS * 9 * WIN * 4;
+        return (size_t)PASTIS_NSYM * pc * 2 + (size_t)SW_WARPS * (pc / 2) * 2 + (size_t)SW_WARPS * 9 * WIN * 4;
     };
     while (prow_cap > STRIPE1 && shm_for(prow_cap) + 1024 > ctx->smem_optin) prow_cap -= STRIPE1;
     const size_t shm1 = shm_for(prow_cap);

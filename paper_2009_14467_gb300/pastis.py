@@ -102,6 +102,8 @@ def lib():
                 "pastis_substitute_kmers": [P, P, i64, ctypes.POINTER(c_params), P, P],
                 "pastis_overlap_spgemm": [P, ctypes.POINTER(c_kmat), ctypes.POINTER(c_params), P, i64,
                                           ctypes.POINTER(i64)],
+                "pastis_overlap_spgemm_rows": [P, ctypes.POINTER(c_kmat), ctypes.POINTER(c_params), i32, i32, P,
+                                               i64, ctypes.POINTER(i64)],
                 "pastis_align_pairs": [P, P, P, i32, P, i64, ctypes.POINTER(c_params), P, P],
                 "pastis_filter_edges": [P, P, i32, P, P, i64, ctypes.POINTER(c_params), P, i64,
                                         ctypes.POINTER(i64)],
@@ -250,18 +252,23 @@ def substitute_kmers(ctx: Context, roots: torch.Tensor, params: Params):
     return code, dist
 
 
-def overlap_spgemm(ctx: Context, A: KMat, params: Params, capacity: int = 0) -> torch.Tensor:
-    """pastis_overlap_spgemm: candidate records (uint8 [n, 20]) sorted by (i, j)."""
+def overlap_spgemm(ctx: Context, A: KMat, params: Params, capacity: int = 0, rows=None) -> torch.Tensor:
+    """pastis_overlap_spgemm (or, with rows=(i0, i1), pastis_overlap_spgemm_rows): candidate
+    records (uint8 [n, 20]) sorted by (i, j)."""
     p = params.c()
     cm = A.c()
     nout = ctypes.c_int64()
+    r0, r1 = (0, A.n_rows) if rows is None else (int(rows[0]), int(rows[1]))
+
+    def call(buf, cap):
+        return lib().pastis_overlap_spgemm_rows(ctx.h, ctypes.byref(cm), ctypes.byref(p), r0, r1, _ptr(buf),
+                                                cap, ctypes.byref(nout))
+
     out = torch.empty((max(capacity, 1), REC_BYTES), dtype=torch.uint8, device=A.row_ptr.device)
-    st = lib().pastis_overlap_spgemm(ctx.h, ctypes.byref(cm), ctypes.byref(p), _ptr(out), capacity,
-                                     ctypes.byref(nout))
+    st = call(out, capacity)
     if st == ERR_CAPACITY:
         out = torch.empty((max(nout.value, 1), REC_BYTES), dtype=torch.uint8, device=A.row_ptr.device)
-        st = lib().pastis_overlap_spgemm(ctx.h, ctypes.byref(cm), ctypes.byref(p), _ptr(out), nout.value,
-                                         ctypes.byref(nout))
+        st = call(out, nout.value)
     _check("pastis_overlap_spgemm", st)
     return out[:nout.value]
 
@@ -299,11 +306,12 @@ def to_records(t: torch.Tensor, dtype: np.dtype) -> np.ndarray:
 
 
 def run(ctx: Context, ascii_dev: torch.Tensor, offsets_dev: torch.Tensor, params: Params,
-        cells: torch.Tensor = None) -> dict:
-    """The whole path a1..a10 on the device."""
+        cells: torch.Tensor = None, rows=None) -> dict:
+    """The whole path a1..a10 on the device; rows=(i0, i1) limits the candidates to the
+    queries i0 <= i < i1 (against every j > i)."""
     codes = encode(ctx, ascii_dev)
     A = build_kmers(ctx, codes, offsets_dev, params.k)
-    cands = overlap_spgemm(ctx, A, params)
+    cands = overlap_spgemm(ctx, A, params, rows=rows)
     alns = align_pairs(ctx, codes, offsets_dev, cands, params, cells)
     edges = filter_edges(ctx, offsets_dev, cands, alns, params)
     return dict(codes=codes, A=A, cands=cands, alns=alns, edges=edges)

@@ -262,3 +262,14 @@ def test_profiler_counts_kernels(P, ctx):
         for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_items", "sw_pass1", "sw_pass3",
                      "filter_flags"):
             assert name in prof and prof[name][0] >= 1 and prof[name][1] >= 0.0, name
+
+
+def test_spgemm_row_blocks_concatenate(P, ctx):
+    ps = synth.zipf_100k(n=2000).subset(np.arange(400))
+    codes = O.encode(ps.ascii)
+    A = P.build_kmers(ctx, dev(codes), dev(ps.offsets), 6)
+    params = P.Params(matrix=MAT, m_subs=25)
+    whole = P.to_records(P.overlap_spgemm(ctx, A, params), P.CAND_DTYPE)
+    parts = [P.to_records(P.overlap_spgemm(ctx, A, params, rows=(a, b)), P.CAND_DTYPE)
+             for a, b in ((0, 37), (37, 37), (37, 250), (250, 400))]
+    assert np.concatenate(parts).tobytes() == whole.tobytes()
