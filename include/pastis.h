@@ -238,6 +238,41 @@ pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets, int
                                   int64_t n_pairs, const pastis_params *params,
                                   pastis_edge *d_out, int64_t capacity, int64_t *n_out);
 
+/* ---- learned prefilter (SURVEY next row; no counterpart in the paper's method) ----
+ * A 16 -> 256 -> 256 -> 1 MLP over per-pair features predicts whether a candidate's
+ * alignment will pass the filter, so that predicted failures skip alignment.  It is
+ * the learned analogue of the paper's common-k-mer threshold (Sec. VI, which trades
+ * 2-3% recall for > 90% fewer alignments, Sec. VI-B).  Weights are float32 masters
+ * with bf16 copies used by the tensor-core kernels (f32 accumulation).  All buffers
+ * are caller-owned device memory; sizes: NW1 = 16*256, NW2 = 256*256, NW3 = 256.
+ * Layouts: w1[i*256 + o], w2[i*256 + o] (input-major), w3[i], b1[256], b2[256], b3[1];
+ * grad / adam_m / adam_v each hold NW1 + 256 + NW2 + 256 + NW3 + 1 floats laid out as
+ * w1, b1, w2, b2, w3, b3.                                                               */
+typedef struct pastis_mlp {
+    float *w1, *b1, *w2, *b2, *w3, *b3;
+    void *w1b, *w2b, *w3b;       /* __nv_bfloat16 copies of w1, w2, w3 */
+    float *grad, *adam_m, *adam_v;
+    int64_t step;                /* Adam steps taken (updated by train_step) */
+} pastis_mlp;
+
+/* Features of each candidate, d_x[n_pairs * 16] as bf16 (row-major). */
+pastis_status pastis_pair_features(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets,
+                                   const pastis_cand *d_pairs, int64_t n_pairs,
+                                   const pastis_params *params, void *d_x);
+/* Logits d_logits[n] of d_x[n * 16] (bf16).  Does not synchronise. */
+pastis_status pastis_mlp_forward(pastis_ctx *ctx, const pastis_mlp *net, const void *d_x, int64_t n,
+                                 float *d_logits);
+/* One Adam step (lr, beta 0.9/0.999) on the weighted logistic loss of d_x[n * 16]
+ * against labels d_y[n] in {0, 1}; positives weigh pos_weight.  n <= 2^22.  *d_loss
+ * (device, optional) receives the mean loss.  Does not synchronise.                */
+pastis_status pastis_mlp_train_step(pastis_ctx *ctx, pastis_mlp *net, const void *d_x, const float *d_y,
+                                    int64_t n, float lr, float pos_weight, float *d_loss);
+/* The candidates whose logit >= threshold, in input order (capacity protocol as for
+ * the other variable-size outputs).  Synchronises.                                   */
+pastis_status pastis_prefilter_select(pastis_ctx *ctx, const pastis_cand *d_pairs, const float *d_logits,
+                                      int64_t n_pairs, float threshold, pastis_cand *d_out,
+                                      int64_t capacity, int64_t *n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ enum ws_slot {
     WS_SPG_RESULT,
     WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER,
     WS_FILT_FLAGS, WS_FILT_SCAN,
+    WS_MLP,
     WS_COUNT
 };
 
