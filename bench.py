@@ -195,6 +195,117 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------
+# learned prefilter vs plain (SURVEY next row f2)
+# ---------------------------------------------------------------------------------
+def run_prefilter(args):
+    """Trains the MLP on pass/fail labels of the exact path over one row block of the
+    100k set, calibrates the threshold for the recall target on a second block, then
+    times plain vs prefiltered on further blocks and reports recall against the exact
+    edges of the same blocks."""
+    import torch
+    import paper_2009_14467_gb300 as P
+    from paper_2009_14467_gb300 import prefilter as F
+    dev = torch.device("cuda", 0)
+    name = args.workload
+    w = WORKLOADS[name]
+    ps = make_set(name)
+    params = P.Params(matrix=synth.blosum62(), k=6, m_subs=w["m"], mode=w["mode"])
+    a = torch.from_numpy(ps.ascii).to(dev)
+    o = torch.from_numpy(ps.offsets).to(dev)
+    ctx = P.Context(0)
+    batches = args.batches or 16
+    blocks = row_blocks(ps.n, batches)
+
+    def exact(rows):
+        codes = P.encode(ctx, a)
+        A = P.build_kmers(ctx, codes, o, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=rows)
+        alns = P.align_pairs(ctx, codes, o, cands, params)
+        edges = P.filter_edges(ctx, o, cands, alns, params)
+        return codes, cands, alns, edges
+
+    t0 = time.perf_counter()
+    codes, cands, alns, _ = exact(blocks[0])
+    y = F.labels_from(alns)
+    x = F.features(ctx, codes, o, cands, params)
+    n = x.shape[0]
+    g = torch.Generator(device=dev).manual_seed(7)
+    take = torch.randperm(n, device=dev, generator=g)[:min(n, args.train_pairs)]
+    xt, yt = x[take].contiguous(), y[take].contiguous()
+    net = F.MLP(seed=11)
+    hist = F.train(ctx, net, xt, yt, epochs=3, batch=65536, lr=2e-3, seed=13)
+    train_s = time.perf_counter() - t0
+    # calibration block
+    codes, cands, alns, _ = exact(blocks[1])
+    yc = F.labels_from(alns)
+    zc = F.forward(ctx, net, F.features(ctx, codes, o, cands, params))
+    thr = F.threshold_for_recall(zc, yc, args.calib_recall)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1000.0
+
+    def plain(rows):
+        return P.run(ctx, a, o, params, rows=rows)
+
+    def prefiltered(rows):
+        codes = P.encode(ctx, a)
+        A = P.build_kmers(ctx, codes, o, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=rows)
+        z = F.forward(ctx, net, F.features(ctx, codes, o, cands, params))
+        kept = F.select(ctx, cands, z, thr)
+        alns = P.align_pairs(ctx, codes, o, kept, params)
+        edges = P.filter_edges(ctx, o, kept, alns, params)
+        return dict(cands=cands, kept=kept, edges=edges)
+
+    eval_blocks = [blocks[k] for k in range(2, min(batches, 2 + max(args.steps, 1)))]
+    for rows in eval_blocks[:1]:          # warm-up of both forms
+        plain(rows)
+        prefiltered(rows)
+    t_plain = t_pref = 0.0
+    e_plain = e_pref = c_all = c_kept = 0
+    missing = 0
+    for rows in eval_blocks:
+        rp, tp = timed(lambda: plain(rows))
+        rf, tf = timed(lambda: prefiltered(rows))
+        t_plain += tp
+        t_pref += tf
+        ep = P.to_records(rp["edges"], P.EDGE_DTYPE)
+        ef = P.to_records(rf["edges"], P.EDGE_DTYPE)
+        e_plain += len(ep)
+        e_pref += len(ef)
+        c_all += rp["cands"].shape[0]
+        c_kept += rf["kept"].shape[0]
+        kp = set(zip(ep["i"].tolist(), ep["j"].tolist()))
+        missing += sum(1 for i, j in zip(ef["i"].tolist(), ef["j"].tolist()) if (i, j) not in kp)
+    recall = e_pref / max(e_plain, 1)
+    line_ok = recall >= args.recall
+    v_plain = e_plain / t_plain
+    v_pref = e_pref / t_pref
+    line = {"metric": "prefilter speedup vs plain at >= 99.5% edge recall (edges/s ratio)",
+            "value": v_pref / v_plain, "unit": "x", "higher_is_better": True, "n_gpus": 1,
+            "steps": len(eval_blocks), "warmup": 1, "dtype": "bf16 (MLP) / int32 (alignment)", "data": "synthetic",
+            "config": {"workload": w["desc"], "name": name, "batch": f"{len(eval_blocks)} of {batches} equal-work row blocks",
+                       "train": f"{xt.shape[0]} labelled candidates of block 0, 3 epochs, Adam 2e-3",
+                       "calibration": f"threshold {thr:.4f} for recall {args.calib_recall} on block 1 "
+                                      f"(target {args.recall} on the evaluation blocks)"},
+            "recall_target_met": None,
+            "edges_per_s_plain": v_plain, "edges_per_s_prefiltered": v_pref, "edge_recall": recall,
+            "edges_not_in_exact": missing, "aligned_pair_reduction": 1.0 - c_kept / max(c_all, 1),
+            "candidates": c_all, "kept": c_kept, "train_s": train_s, "train_loss": hist}
+    line["recall_target_met"] = line_ok
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
 def main():
@@ -209,11 +320,19 @@ def main():
                     help="equal-work query-row blocks the job is split into (default: 8 for 100k sets, else 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
+    ap.add_argument("--mode", default="plain", choices=["plain", "prefilter"],
+                    help="plain: the exact path (the headline); prefilter: learned prefilter vs plain")
+    ap.add_argument("--recall", type=float, default=0.995, help="edge recall the prefilter must keep")
+    ap.add_argument("--calib-recall", type=float, default=0.998,
+                    help="recall the threshold is calibrated for on the calibration block (margin over --recall)")
+    ap.add_argument("--train-pairs", type=int, default=10_000_000)
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "prefilter":
+        return run_prefilter(args)
 
     import torch
     import torch.distributed as dist
