@@ -207,6 +207,14 @@ pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pastis_kmat *A,
                                          int32_t row_end, pastis_cand *d_out, int64_t capacity,
                                          int64_t *n_out);
 
+/* Serving form: query sequences (rows of Q) against a database (columns = every
+ * sequence of DB, not only j > i); pair (i, j) names query i and database entry j.
+ * Exact k-mers only (params->m_subs == 0, else PASTIS_ERR_UNSUPPORTED).  Q and DB are
+ * each built by pastis_build_kmers.  Output sorted by (i, j).  Synchronises.        */
+pastis_status pastis_query_overlap(pastis_ctx *ctx, const pastis_kmat *Q, const pastis_kmat *DB,
+                                   const pastis_params *params, pastis_cand *d_out, int64_t capacity,
+                                   int64_t *n_out);
+
 /* ---- a8-a9: alignment (Sec. IV-E) ---------------------------------------------- */
 
 /* One record per candidate, d_out[n_pairs].
@@ -227,6 +235,14 @@ pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_codes,
                                  const pastis_cand *d_pairs, int64_t n_pairs,
                                  const pastis_params *params, pastis_aln *d_out,
                                  int64_t *d_cells);
+
+/* The same with the queries' and targets' residues in separate arrays: pair (i, j)
+ * aligns query i of (d_qcodes, d_qoffsets[n_q+1]) with target j of (d_tcodes,
+ * d_toffsets[n_t+1]) -- the serving form, database resident and queries per batch.  */
+pastis_status pastis_align_pairs_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                    int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                    int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
+                                    const pastis_params *params, pastis_aln *d_out, int64_t *d_cells);
 
 /* ---- a10: similarity filter (Sec. IV-F, VI-B) ----------------------------------- */
 
@@ -272,6 +288,12 @@ pastis_status pastis_mlp_train_step(pastis_ctx *ctx, pastis_mlp *net, const void
 pastis_status pastis_prefilter_select(pastis_ctx *ctx, const pastis_cand *d_pairs, const float *d_logits,
                                       int64_t n_pairs, float threshold, pastis_cand *d_out,
                                       int64_t capacity, int64_t *n_out);
+
+/* The filter with queries and targets in separate offset arrays (serving form). */
+pastis_status pastis_filter_edges_qt(pastis_ctx *ctx, const int64_t *d_qoffsets, int32_t n_q,
+                                     const int64_t *d_toffsets, int32_t n_t, const pastis_cand *d_pairs,
+                                     const pastis_aln *d_alns, int64_t n_pairs, const pastis_params *params,
+                                     pastis_edge *d_out, int64_t capacity, int64_t *n_out);
 
 #ifdef __cplusplus
 }

@@ -13,9 +13,9 @@
 
 #include "internal.cuh"
 
-pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets, const pastis_cand *d_pairs,
-                       int64_t n_pairs, const pastis_params *p, const int8_t *dmat, int *flags, int lmax,
-                       pastis_aln *d_out, int64_t *d_cells);
+pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, const uint8_t *d_tcodes,
+                       const int64_t *d_toffsets, const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *p,
+                       const int8_t *dmat, int *flags, int lmax, pastis_aln *d_out, int64_t *d_cells);
 
 namespace {
 
@@ -131,7 +131,8 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
     res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
 }
 
-__global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *codes, const int64_t *offsets,
+__global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, const int64_t *qoffsets,
+                                                        const uint8_t *tcodes, const int64_t *toffsets,
                                                         const pastis_cand *pairs, int64_t n_pairs, int k,
                                                         const int8_t *gmat, int o, int e, int X, int32_t *gbuf,
                                                         int W, int *next_task, ext_out *out) {
@@ -157,14 +158,14 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *codes, co
         r.score = 0; r.a = 0; r.b = 0; r.carry = 0; r.cells = 0;
         const bool has = seed == 0 || (c.count >= 2 && c.qpos[1] != 0xFFFF);
         if (has) {
-            const int64_t qo = offsets[c.i], to = offsets[c.j];
-            const int lq = (int)(offsets[c.i + 1] - qo), lt = (int)(offsets[c.j + 1] - to);
+            const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
+            const int lq = (int)(qoffsets[c.i + 1] - qo), lt = (int)(toffsets[c.j + 1] - to);
             const int pi = c.qpos[seed], pj = c.tpos[seed];
             if (!left)
-                xd_extend_warp(codes + qo + pi + k, lq - pi - k, 1, codes + to + pj + k, lt - pj - k, 1, s_mat, o,
+                xd_extend_warp(qcodes + qo + pi + k, lq - pi - k, 1, tcodes + to + pj + k, lt - pj - k, 1, s_mat, o,
                                e, X, buf, W, &r);
             else
-                xd_extend_warp(codes + qo + pi - 1, pi, -1, codes + to + pj - 1, pj, -1, s_mat, o, e, X, buf, W,
+                xd_extend_warp(qcodes + qo + pi - 1, pi, -1, tcodes + to + pj - 1, pj, -1, s_mat, o, e, X, buf, W,
                                &r);
         }
         if (lane == 0) out[task] = r;
@@ -172,15 +173,16 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *codes, co
     }
 }
 
-__global__ void k_xd_combine(const uint8_t *codes, const int64_t *offsets, const pastis_cand *pairs,
+__global__ void k_xd_combine(const uint8_t *qcodes, const int64_t *qoffsets, const uint8_t *tcodes,
+                             const int64_t *toffsets, const pastis_cand *pairs,
                              int64_t n_pairs, int k, const int8_t *gmat, int ani, int cov, const ext_out *ext,
                              pastis_aln *out, unsigned long long *cells) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long my = 0;
     if (p < n_pairs) {
         const pastis_cand c = pairs[p];
-        const int64_t qo = offsets[c.i], to = offsets[c.j];
-        const int lq = (int)(offsets[c.i + 1] - qo), lt = (int)(offsets[c.j + 1] - to);
+        const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
+        const int lq = (int)(qoffsets[c.i + 1] - qo), lt = (int)(toffsets[c.j + 1] - to);
         const int ns = (c.count >= 2 && c.qpos[1] != 0xFFFF) ? 2 : 1;
         pastis_aln best;
         bool best_ok = false;
@@ -189,7 +191,7 @@ __global__ void k_xd_combine(const uint8_t *codes, const int64_t *offsets, const
             const int pi = c.qpos[s], pj = c.tpos[s];
             int seed = 0, sid = 0;
             for (int x = 0; x < k; ++x) {
-                const int a = codes[qo + pi + x], b = codes[to + pj + x];
+                const int a = qcodes[qo + pi + x], b = tcodes[to + pj + x];
                 seed += gmat[a * PASTIS_NSYM + b];
                 sid += (a == b);
             }
@@ -234,14 +236,14 @@ __global__ void k_check_codes(const uint8_t *codes, int64_t n, int *bad) {
         if (codes[x] >= PASTIS_NSYM) *bad = 1;
 }
 
-__global__ void k_check_pairs(const pastis_cand *pairs, int64_t n_pairs, const int64_t *offsets, int32_t n_seq,
-                              int k, int xd, int *bad) {
+__global__ void k_check_pairs(const pastis_cand *pairs, int64_t n_pairs, const int64_t *qoffsets, int32_t n_q,
+                              const int64_t *toffsets, int32_t n_t, int k, int xd, int *bad) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
     const pastis_cand c = pairs[p];
-    if (c.i < 0 || c.j < 0 || c.i >= n_seq || c.j >= n_seq) { *bad = 1; return; }
+    if (c.i < 0 || c.j < 0 || c.i >= n_q || c.j >= n_t) { *bad = 1; return; }
     if (!xd) return;
-    const int lq = (int)(offsets[c.i + 1] - offsets[c.i]), lt = (int)(offsets[c.j + 1] - offsets[c.j]);
+    const int lq = (int)(qoffsets[c.i + 1] - qoffsets[c.i]), lt = (int)(toffsets[c.j + 1] - toffsets[c.j]);
     const int ns = (c.count >= 2 && c.qpos[1] != 0xFFFF) ? 2 : 1;
     for (int s = 0; s < ns; ++s)
         if ((int)c.qpos[s] + k > lq || (int)c.tpos[s] + k > lt) *bad = 1;
@@ -249,36 +251,44 @@ __global__ void k_check_pairs(const pastis_cand *pairs, int64_t n_pairs, const i
 
 }  // namespace
 
-extern "C" pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets,
-                                            int32_t n_seqs, const pastis_cand *d_pairs, int64_t n_pairs,
-                                            const pastis_params *params, pastis_aln *d_out, int64_t *d_cells) {
-    if (!ctx || n_pairs < 0 || n_seqs < 0) return PASTIS_ERR_INVALID_ARG;
+static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, int32_t n_q,
+                              const uint8_t *d_tcodes, const int64_t *d_toffsets, int32_t n_t,
+                              const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *params,
+                              pastis_aln *d_out, int64_t *d_cells) {
+    if (!ctx || n_pairs < 0 || n_q < 0 || n_t < 0) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
     if (n_pairs == 0) return PASTIS_OK;
-    if (!d_codes || !d_offsets || !d_pairs || !d_out || n_seqs == 0) return PASTIS_ERR_INVALID_ARG;
+    if (!d_qcodes || !d_qoffsets || !d_tcodes || !d_toffsets || !d_pairs || !d_out || n_q == 0 || n_t == 0)
+        return PASTIS_ERR_INVALID_ARG;
     cudaStream_t st = ctx->stream;
     int8_t *dmat;
     PASTIS_WS(dmat, ctx, WS_FLAGS, 1024);
-    int *flags = (int *)(dmat + 768);   // [0] error, [1] [3] pair counters, [2] max length, [4] bad pair,
+    int *flags = (int *)(dmat + 768);   // [0] error, [1] [3] [8] pair counters, [2] max length, [4] bad pair,
                                         // [5] bad code, [6..7] task counter
     PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, params->matrix, 576, cudaMemcpyHostToDevice, st));
     PASTIS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64, st));
     const int xd = params->mode == PASTIS_XD;
-    k_max_len<<<(unsigned)ceil_div64(n_seqs, 256), 256, 0, st>>>(d_offsets, n_seqs, flags + 2);
+    k_max_len<<<(unsigned)ceil_div64(n_q, 256), 256, 0, st>>>(d_qoffsets, n_q, flags + 2);
     PASTIS_LAUNCHED(ctx);
-    k_check_pairs<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_offsets, n_seqs,
-                                                                     params->k, xd, flags + 4);
+    k_max_len<<<(unsigned)ceil_div64(n_t, 256), 256, 0, st>>>(d_toffsets, n_t, flags + 2);
     PASTIS_LAUNCHED(ctx);
-    int64_t h_off_end = 0;
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_off_end, d_offsets + n_seqs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    k_check_pairs<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, n_q, d_toffsets,
+                                                                     n_t, params->k, xd, flags + 4);
+    PASTIS_LAUNCHED(ctx);
+    int64_t h_end[2] = {0, 0};
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_end[0], d_qoffsets + n_q, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_end[1], d_toffsets + n_t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h_off_end > 0) {
-        int blocks_c = (int)std::min<int64_t>(ceil_div64(h_off_end, 256), (int64_t)ctx->sm_count * 16);
-        prof_begin(ctx, "align_checks");
-        k_check_codes<<<blocks_c, 256, 0, st>>>(d_codes, h_off_end, flags + 5);
-        PASTIS_LAUNCHED(ctx);
-        prof_end(ctx);
+    for (int w = 0; w < 2; ++w) {
+        const uint8_t *cd = w == 0 ? d_qcodes : d_tcodes;
+        if (h_end[w] > 0 && (w == 0 || cd != d_qcodes)) {
+            int blocks_c = (int)std::min<int64_t>(ceil_div64(h_end[w], 256), (int64_t)ctx->sm_count * 16);
+            prof_begin(ctx, "align_checks");
+            k_check_codes<<<blocks_c, 256, 0, st>>>(cd, h_end[w], flags + 5);
+            PASTIS_LAUNCHED(ctx);
+            prof_end(ctx);
+        }
     }
     int hf[6];
     PASTIS_CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
@@ -290,7 +300,8 @@ extern "C" pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_co
     const int blocks = ctx->sm_count * 2;
     const int nwarps = blocks * ALN_WARPS;
     if (!xd) {
-        s = sw_align(ctx, d_codes, d_offsets, d_pairs, n_pairs, params, dmat, flags, lmax, d_out, d_cells);
+        s = sw_align(ctx, d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params, dmat, flags, lmax,
+                     d_out, d_cells);
         if (s != PASTIS_OK) return s;
     } else {
         const int W = lmax + 2;
@@ -299,15 +310,15 @@ extern "C" pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_co
         ext_out *ext;
         PASTIS_WS(ext, ctx, WS_ALN_PASS1, sizeof(ext_out) * 4 * (size_t)n_pairs);
         prof_begin(ctx, "xd_extend");
-        k_xd_ext<<<blocks, ALN_THREADS, 0, st>>>(d_codes, d_offsets, d_pairs, n_pairs, params->k, dmat,
-                                                 params->gap_open, params->gap_extend, params->xdrop, gbuf, W,
-                                                 flags + 6, ext);
+        k_xd_ext<<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs,
+                                                 params->k, dmat, params->gap_open, params->gap_extend, params->xdrop,
+                                                 gbuf, W, flags + 6, ext);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
         prof_begin(ctx, "xd_combine");
         k_xd_combine<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(
-            d_codes, d_offsets, d_pairs, n_pairs, params->k, dmat, params->ani_min_pct, params->cov_min_pct, ext,
-            d_out, (unsigned long long *)d_cells);
+            d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat, params->ani_min_pct,
+            params->cov_min_pct, ext, d_out, (unsigned long long *)d_cells);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
     }
@@ -315,4 +326,19 @@ extern "C" pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_co
     PASTIS_CUDA_TRY(cudaMemcpyAsync(&herr, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
     return herr ? PASTIS_ERR_INTERNAL : PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_align_pairs(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets,
+                                            int32_t n_seqs, const pastis_cand *d_pairs, int64_t n_pairs,
+                                            const pastis_params *params, pastis_aln *d_out, int64_t *d_cells) {
+    return align_qt(ctx, d_codes, d_offsets, n_seqs, d_codes, d_offsets, n_seqs, d_pairs, n_pairs, params, d_out,
+                    d_cells);
+}
+
+extern "C" pastis_status pastis_align_pairs_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                               int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                               int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
+                                               const pastis_params *params, pastis_aln *d_out, int64_t *d_cells) {
+    return align_qt(ctx, d_qcodes, d_qoffsets, n_q, d_tcodes, d_toffsets, n_t, d_pairs, n_pairs, params, d_out,
+                    d_cells);
 }

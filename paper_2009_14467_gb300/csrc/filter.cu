@@ -16,13 +16,14 @@ __device__ __forceinline__ bool keeps(const pastis_aln &a, int lq, int lt, int a
     return 100 * (int)a.ident >= ani * (int)a.cols && 100 * span >= cov * L;
 }
 
-__global__ void k_filter_flags(const int64_t *offsets, int32_t n_seqs, const pastis_cand *pairs,
-                               const pastis_aln *alns, int64_t n, int ani, int cov, uint32_t *flags, int *bad) {
+__global__ void k_filter_flags(const int64_t *qoffsets, int32_t n_q, const int64_t *toffsets, int32_t n_t,
+                               const pastis_cand *pairs, const pastis_aln *alns, int64_t n, int ani, int cov,
+                               uint32_t *flags, int *bad) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const pastis_cand c = pairs[p];
-    if (c.i < 0 || c.j < 0 || c.i >= n_seqs || c.j >= n_seqs) { *bad = 1; flags[p] = 0; return; }
-    const int lq = (int)(offsets[c.i + 1] - offsets[c.i]), lt = (int)(offsets[c.j + 1] - offsets[c.j]);
+    if (c.i < 0 || c.j < 0 || c.i >= n_q || c.j >= n_t) { *bad = 1; flags[p] = 0; return; }
+    const int lq = (int)(qoffsets[c.i + 1] - qoffsets[c.i]), lt = (int)(toffsets[c.j + 1] - toffsets[c.j]);
     flags[p] = keeps(alns[p], lq, lt, ani, cov) ? 1u : 0u;
 }
 
@@ -43,16 +44,15 @@ __global__ void k_filter_scatter(const pastis_cand *pairs, const pastis_aln *aln
 
 }  // namespace
 
-extern "C" pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets, int32_t n_seqs,
-                                             const pastis_cand *d_pairs, const pastis_aln *d_alns, int64_t n_pairs,
-                                             const pastis_params *params, pastis_edge *d_out, int64_t capacity,
-                                             int64_t *n_out) {
-    if (!ctx || !n_out || n_pairs < 0 || capacity < 0 || n_seqs < 0) return PASTIS_ERR_INVALID_ARG;
+static pastis_status filter_qt(pastis_ctx *ctx, const int64_t *d_qoffsets, int32_t n_q, const int64_t *d_toffsets,
+                               int32_t n_t, const pastis_cand *d_pairs, const pastis_aln *d_alns, int64_t n_pairs,
+                               const pastis_params *params, pastis_edge *d_out, int64_t capacity, int64_t *n_out) {
+    if (!ctx || !n_out || n_pairs < 0 || capacity < 0 || n_q < 0 || n_t < 0) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
     *n_out = 0;
     if (n_pairs == 0) return PASTIS_OK;
-    if (!d_offsets || !d_pairs || !d_alns) return PASTIS_ERR_INVALID_ARG;
+    if (!d_qoffsets || !d_toffsets || !d_pairs || !d_alns) return PASTIS_ERR_INVALID_ARG;
     if (n_pairs > 0xFFFFFFFFll) return PASTIS_ERR_UNSUPPORTED;
     cudaStream_t st = ctx->stream;
     uint32_t *flags;
@@ -62,8 +62,8 @@ extern "C" pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_o
     PASTIS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
     const unsigned blocks = (unsigned)ceil_div64(n_pairs, 256);
     prof_begin(ctx, "filter_flags");
-    k_filter_flags<<<blocks, 256, 0, st>>>(d_offsets, n_seqs, d_pairs, d_alns, n_pairs, params->ani_min_pct,
-                                           params->cov_min_pct, flags, bad);
+    k_filter_flags<<<blocks, 256, 0, st>>>(d_qoffsets, n_q, d_toffsets, n_t, d_pairs, d_alns, n_pairs,
+                                           params->ani_min_pct, params->cov_min_pct, flags, bad);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     s = exclusive_scan_u32(ctx, flags, off, n_pairs);
@@ -84,4 +84,19 @@ extern "C" pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_o
     prof_end(ctx);
     PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
     return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets, int32_t n_seqs,
+                                             const pastis_cand *d_pairs, const pastis_aln *d_alns, int64_t n_pairs,
+                                             const pastis_params *params, pastis_edge *d_out, int64_t capacity,
+                                             int64_t *n_out) {
+    return filter_qt(ctx, d_offsets, n_seqs, d_offsets, n_seqs, d_pairs, d_alns, n_pairs, params, d_out, capacity,
+                     n_out);
+}
+
+extern "C" pastis_status pastis_filter_edges_qt(pastis_ctx *ctx, const int64_t *d_qoffsets, int32_t n_q,
+                                                const int64_t *d_toffsets, int32_t n_t, const pastis_cand *d_pairs,
+                                                const pastis_aln *d_alns, int64_t n_pairs, const pastis_params *params,
+                                                pastis_edge *d_out, int64_t capacity, int64_t *n_out) {
+    return filter_qt(ctx, d_qoffsets, n_q, d_toffsets, n_t, d_pairs, d_alns, n_pairs, params, d_out, capacity, n_out);
 }

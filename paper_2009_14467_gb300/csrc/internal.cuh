@@ -43,7 +43,7 @@ struct pastis_ctx {
     size_t smem_optin;
     // kept result of the last overlap product (two-phase size protocol)
     int64_t spg_n;
-    const void *spg_key_a;
+    const void *spg_key_a, *spg_key_b;
     int64_t spg_key_nnz;
     int32_t spg_key_m, spg_key_min, spg_key_k, spg_key_r0, spg_key_r1;
     uint32_t spg_key_mat_hash;

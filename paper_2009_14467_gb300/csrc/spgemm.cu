@@ -238,21 +238,28 @@ size_t table_bytes(int tsize, bool subs) {
 
 }  // namespace
 
-extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pastis_kmat *A,
-                                                    const pastis_params *params, int32_t row_begin, int32_t row_end,
-                                                    pastis_cand *d_out, int64_t capacity, int64_t *n_out) {
+// The product driver.  Self mode (DB == nullptr): rows of A against A's postings,
+// columns j > i.  Query mode: rows of A (the queries) against the postings of DB,
+// every column j of DB (exact k-mers only).
+static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const pastis_kmat *DB,
+                                  const pastis_params *params, int32_t row_begin, int32_t row_end, pastis_cand *d_out,
+                                  int64_t capacity, int64_t *n_out) {
     if (!ctx || !A || !n_out || capacity < 0) return PASTIS_ERR_INVALID_ARG;
     if (row_begin < 0 || row_end < row_begin || row_end > A->n_rows) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
     if (A->k != params->k || A->n_rows < 0) return PASTIS_ERR_INVALID_ARG;
+    const bool self = DB == nullptr;
+    if (!self && (DB->k != params->k || params->m_subs != 0)) return self ? PASTIS_ERR_INVALID_ARG : PASTIS_ERR_UNSUPPORTED;
     cudaStream_t st = ctx->stream;
     const int32_t n = A->n_rows;
+    const int32_t n_cols = self ? n : DB->n_rows;
     const bool subs = params->m_subs > 0;
     const uint32_t mh = params_matrix_hash(params);
+    const void *key_b = self ? nullptr : (const void *)DB->col_ptr;
 
     // a kept result for the same inputs: copy it (two-phase size protocol)
-    if (ctx->spg_valid && ctx->spg_key_a == (const void *)A->row_ptr && ctx->spg_key_nnz == A->nnz &&
+    if (ctx->spg_valid && ctx->spg_key_b == key_b && ctx->spg_key_a == (const void *)A->row_ptr && ctx->spg_key_nnz == A->nnz &&
         ctx->spg_key_m == params->m_subs && ctx->spg_key_min == params->min_shared &&
         ctx->spg_key_k == params->k && ctx->spg_key_mat_hash == (subs ? mh : 0u) &&
         ctx->spg_key_r0 == row_begin && ctx->spg_key_r1 == row_end) {
@@ -267,14 +274,15 @@ extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pasti
         return PASTIS_OK;
     }
     ctx->spg_valid = 0;
-    if (n < 2 || A->nnz == 0) {
+    if ((self && n < 2) || (!self && (n < 1 || n_cols < 1)) || A->nnz == 0 || (!self && DB->nnz == 0)) {
         *n_out = 0;
         return PASTIS_OK;
     }
 
     operand F, Bop;
     F.row_ptr = A->row_ptr; F.row_code = A->row_code; F.row_pos = A->row_pos;
-    F.col_ptr = A->col_ptr; F.col_seq = A->col_seq; F.col_pos = A->col_pos;
+    const pastis_kmat *C = self ? A : DB;
+    F.col_ptr = C->col_ptr; F.col_seq = C->col_seq; F.col_pos = C->col_pos;
     Bop = F;
     if (subs) {
         as_matrix AS;
@@ -312,22 +320,24 @@ extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pasti
     struct plan_item { int32_t i, j0, j1; int tlog; int64_t cap; };
     std::vector<plan_item> plan;
     plan.reserve((size_t)n);
-    for (int32_t i = row_begin; i < row_end && i + 1 < n; ++i) {
+    for (int32_t i = row_begin; i < row_end; ++i) {
+        const int32_t jlo = self ? i + 1 : 0;
+        if (jlo >= n_cols) continue;
         int64_t b = hb[i] + (subs ? hb[(size_t)n + i] : 0);
-        int64_t width = n - 1 - i;
+        int64_t width = n_cols - jlo;
         int64_t est = std::min(b, width);
         if (est <= 0) continue;
         if (est * 4 <= (int64_t)tmax * 3) {
             int tl = 6;
             while ((1ll << tl) * 3 < est * 4) ++tl;
-            plan.push_back({i, i + 1, n, tl, est});
+            plan.push_back({i, jlo, n_cols, tl, est});
         } else {
             int tl = 0;
             while ((1 << tl) < tmax) ++tl;
             int64_t pieces = ceil_div64(est * 2, tmax);
             for (int64_t q = 0; q < pieces; ++q) {
-                int32_t a = (int32_t)(i + 1 + (width * q) / pieces);
-                int32_t z = (int32_t)(i + 1 + (width * (q + 1)) / pieces);
+                int32_t a = (int32_t)(jlo + (width * q) / pieces);
+                int32_t z = (int32_t)(jlo + (width * (q + 1)) / pieces);
                 if (z > a) plan.push_back({i, a, z, tl, std::min<int64_t>(std::min<int64_t>(b, z - a), tmax)});
             }
         }
@@ -335,8 +345,10 @@ extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pasti
 
     // upper bound of the records: distinct j per row
     int64_t ubound = 0;
-    for (int32_t i = row_begin; i < row_end && i + 1 < n; ++i)
-        ubound += std::min<int64_t>(hb[i] + (subs ? hb[(size_t)n + i] : 0), (int64_t)(n - 1 - i));
+    for (int32_t i = row_begin; i < row_end; ++i) {
+        const int32_t jlo = self ? i + 1 : 0;
+        if (jlo < n_cols) ubound += std::min<int64_t>(hb[i] + (subs ? hb[(size_t)n + i] : 0), (int64_t)(n_cols - jlo));
+    }
     pastis_cand *result;
     PASTIS_WS(result, ctx, WS_SPG_RESULT, sizeof(pastis_cand) * (size_t)(ubound + 1));
 
@@ -501,6 +513,7 @@ extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pasti
     ctx->spg_key_mat_hash = subs ? mh : 0u;
     ctx->spg_key_r0 = row_begin;
     ctx->spg_key_r1 = row_end;
+    ctx->spg_key_b = key_b;
     *n_out = total;
     if (capacity < total) return PASTIS_ERR_CAPACITY;
     if (total > 0) {
@@ -511,8 +524,21 @@ extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pasti
     return PASTIS_OK;
 }
 
+extern "C" pastis_status pastis_overlap_spgemm_rows(pastis_ctx *ctx, const pastis_kmat *A,
+                                                    const pastis_params *params, int32_t row_begin, int32_t row_end,
+                                                    pastis_cand *d_out, int64_t capacity, int64_t *n_out) {
+    return overlap_impl(ctx, A, nullptr, params, row_begin, row_end, d_out, capacity, n_out);
+}
+
 extern "C" pastis_status pastis_overlap_spgemm(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *params,
                                                pastis_cand *d_out, int64_t capacity, int64_t *n_out) {
     if (!A) return PASTIS_ERR_INVALID_ARG;
-    return pastis_overlap_spgemm_rows(ctx, A, params, 0, A->n_rows, d_out, capacity, n_out);
+    return overlap_impl(ctx, A, nullptr, params, 0, A->n_rows, d_out, capacity, n_out);
+}
+
+extern "C" pastis_status pastis_query_overlap(pastis_ctx *ctx, const pastis_kmat *Q, const pastis_kmat *DB,
+                                              const pastis_params *params, pastis_cand *d_out, int64_t capacity,
+                                              int64_t *n_out) {
+    if (!Q || !DB) return PASTIS_ERR_INVALID_ARG;
+    return overlap_impl(ctx, Q, DB, params, 0, Q->n_rows, d_out, capacity, n_out);
 }

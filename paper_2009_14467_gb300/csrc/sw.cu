@@ -265,7 +265,8 @@ __device__ __forceinline__ int rows_per_lane(int m) {
     return min(16, max(2, (per + 1) & ~1));
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *codes, const int64_t *offsets,
+__global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *qcodes, const int64_t *qoffsets,
+                                                         const uint8_t *tcodes, const int64_t *toffsets,
                                                          const pastis_cand *pairs, const int64_t *seg_start,
                                                          int64_t n_seg, const int8_t *gmat, int o, int e,
                                                          int max_s, int prow_cap, char *scratch, size_t warp_bytes,
@@ -291,15 +292,15 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *codes
         if (sg >= n_seg) break;
         const int64_t p0 = seg_start[sg], p1 = seg_start[sg + 1];
         const int qi = pairs[p0].i;
-        const int64_t qo = offsets[qi];
-        const int m = (int)(offsets[qi + 1] - qo);
+        const int64_t qo = qoffsets[qi];
+        const int m = (int)(qoffsets[qi + 1] - qo);
         const int lr = rows_per_lane(m);
         const int prow = ((m + 32 * lr - 1) / (32 * lr)) * (32 * lr);
         // query profile: prof[c][i] = M[q_i][c], PAD past the end of the query
         if (prow <= prow_cap) {
             for (int x = threadIdx.x; x < PASTIS_NSYM * prow; x += blockDim.x) {
                 const int c = x / prow, i = x - c * prow;
-                s_prof[x] = (int16_t)(i < m ? (int)gmat[codes[qo + i] * PASTIS_NSYM + c] : PAD_SCORE);
+                s_prof[x] = (int16_t)(i < m ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] : PAD_SCORE);
             }
         }
         __syncthreads();
@@ -310,15 +311,15 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *codes
             const int64_t p = p0 + pk;
             if (p >= p1) break;
             const pastis_cand c = pairs[p];
-            const int64_t to = offsets[c.j];
-            const int n = (int)(offsets[c.j + 1] - to);
+            const int64_t to = toffsets[c.j];
+            const int n = (int)(toffsets[c.j + 1] - to);
             sw_score_out r;
             r.score = 0; r.end_i = 0; r.end_j = 0; r.rect_i = 0; r.rect_j = 0; r.big = 0;
             if ((int64_t)max_s * (int64_t)min(m, n) >= 32767 || prow > prow_cap) {
                 r.big = 1;                          // left to the int32 carry pass
             } else if (m > 0 && n > 0) {
                 int bh, bi, bj;
-                const uint8_t *tp = codes + to;
+                const uint8_t *tp = tcodes + to;
 #define PASTIS_SW_CASE(L) \
     case L: score_warp<L>(s_prof, prow, tp, m, n, o, e, my, sstride, bm4, &bh, &bi, &bj); break;
                 switch (lr) {
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *codes
                 if (bh > 0) {
                     r.score = bh; r.end_i = bi; r.end_j = bj;
                     int amax = 0, bmax = 0;
-                    if (bound_warp(codes + qo + bi, bi + 1, tp + bj, bj + 1, s_mat8, o, e, bh, bi, bm4, win,
+                    if (bound_warp(qcodes + qo + bi, bi + 1, tp + bj, bj + 1, s_mat8, o, e, bh, bi, bm4, win,
                                    &amax, &bmax) && amax > 0 && bmax > 0) {
                         r.rect_i = bi + 1 - amax;
                         r.rect_j = bj + 1 - bmax;
@@ -563,7 +564,8 @@ __device__ void finish_record(pastis_aln &rec, int S, int ei, int ej, int qb, in
     rec.passes = (rec.cols > 0 && 100 * ident >= ani * (int)rec.cols && 100 * span >= cov * L) ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, const int64_t *offsets,
+__global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, const int64_t *qoffsets,
+                                                         const uint8_t *tcodes, const int64_t *toffsets,
                                                          const pastis_cand *pairs, int64_t n_pairs,
                                                          const int8_t *gmat, int o, int e, int ani, int cov,
                                                          stripe3_cell *scratch, int sstride, int *next_pair,
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
         // the four pairs of this warp: small rectangles go to the groups together
         const int64_t pg = p0 + grp;
         int gm = 0, gn = 0;
-        const uint8_t *gq = codes, *gt = codes;
+        const uint8_t *gq = qcodes, *gt = tcodes;
         sw_score_out g1;
         g1.score = 0; g1.big = 0; g1.end_i = g1.end_j = g1.rect_i = g1.rect_j = 0;
         if (pg < n_pairs) {
@@ -596,8 +598,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
                 const pastis_cand c = pairs[pg];
                 gm = g1.end_i + 1 - g1.rect_i;
                 gn = g1.end_j + 1 - g1.rect_j;
-                gq = codes + offsets[c.i] + g1.rect_i;
-                gt = codes + offsets[c.j] + g1.rect_j;
+                gq = qcodes + qoffsets[c.i] + g1.rect_i;
+                gt = tcodes + toffsets[c.j] + g1.rect_j;
             }
         }
         int gh;
@@ -605,7 +607,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
         carry_group(gq, gm, gt, gn, s_mat, o, e, &gh, &gb, &gim);
         if (lg == 0 && pg < n_pairs && gm > 0) {
             const pastis_cand c = pairs[pg];
-            const int lq = (int)(offsets[c.i + 1] - offsets[c.i]), lt = (int)(offsets[c.j + 1] - offsets[c.j]);
+            const int lq = (int)(qoffsets[c.i + 1] - qoffsets[c.i]), lt = (int)(toffsets[c.j + 1] - toffsets[c.j]);
             if (gh != g1.score) atomicExch(err, 1);
             pastis_aln rec;
             rec.seed_used = 0; rec.passes = 0; rec.reserved = 0;
@@ -621,8 +623,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
             const bool small = !r1.big && r1.score > 0 && r1.end_i + 1 - r1.rect_i <= GROWS;
             if (small) continue;
             const pastis_cand c = pairs[p];
-            const int64_t qo = offsets[c.i], to = offsets[c.j];
-            const int lq = (int)(offsets[c.i + 1] - qo), lt = (int)(offsets[c.j + 1] - to);
+            const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
+            const int lq = (int)(qoffsets[c.i + 1] - qo), lt = (int)(toffsets[c.j + 1] - to);
             pastis_aln rec;
             rec.score = 0; rec.qb = rec.qe = rec.tb = rec.te = 0; rec.ident = rec.cols = 0;
             rec.seed_used = 0; rec.passes = 0; rec.reserved = 0;
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
                 if (lq > 0 && lt > 0) {
                     int h, bi, bj;
                     uint32_t beg, im;
-                    carry_warp<true>(codes + qo, lq, codes + to, lt, s_mat, o, e, my, sstride, &h, &bi, &bj, &beg, &im);
+                    carry_warp<true>(qcodes + qo, lq, tcodes + to, lt, s_mat, o, e, my, sstride, &h, &bi, &bj, &beg, &im);
                     if (h > 0)
                         finish_record(rec, h, bi, bj, (int)(beg >> 16), (int)(beg & 0xFFFF), (int)(im >> 16),
                                       (int)(im & 0xFFFF), lq, lt, ani, cov);
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
                 const int ri = r1.rect_i, rj = r1.rect_j;
                 int h, dummy_i, dummy_j;
                 uint32_t beg, im;
-                carry_warp<false>(codes + qo + ri, r1.end_i + 1 - ri, codes + to + rj, r1.end_j + 1 - rj, s_mat, o,
+                carry_warp<false>(qcodes + qo + ri, r1.end_i + 1 - ri, tcodes + to + rj, r1.end_j + 1 - rj, s_mat, o,
                                   e, my, sstride, &h, &dummy_i, &dummy_j, &beg, &im);
                 if (h != r1.score && lane == 0) atomicExch(err, 1);
                 finish_record(rec, r1.score, r1.end_i, r1.end_j, ri + (int)(beg >> 16), rj + (int)(beg & 0xFFFF),
@@ -655,7 +657,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *codes, c
 }  // namespace
 
 // Host side of the Smith-Waterman path (called by pastis_align_pairs after validation).
-pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets, const pastis_cand *d_pairs,
+pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, const uint8_t *d_tcodes,
+                       const int64_t *d_toffsets, const pastis_cand *d_pairs,
                        int64_t n_pairs, const pastis_params *p, const int8_t *dmat, int *flags, int lmax,
                        pastis_aln *d_out, int64_t *d_cells) {
     cudaStream_t st = ctx->stream;
@@ -699,13 +702,15 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d
     void *scratch;
     PASTIS_WS(scratch, ctx, WS_ALN_SCRATCH, std::max(scr1, scr3));
     prof_begin(ctx, "sw_pass1");
-    k_sw_score<<<blocks1, SW_THREADS, shm1, st>>>(d_codes, d_offsets, d_pairs, seg_start, (int64_t)h_nseg, dmat,
+    k_sw_score<<<blocks1, SW_THREADS, shm1, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, seg_start,
+                                                  (int64_t)h_nseg, dmat,
                                                   p->gap_open, p->gap_extend, max_s, prow_cap, (char *)scratch,
                                                   warp_bytes, sstride, flags + 1, res, (unsigned long long *)d_cells);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     prof_begin(ctx, "sw_pass3");
-    k_sw_carry<<<blocks3, SW_THREADS, 0, st>>>(d_codes, d_offsets, d_pairs, n_pairs, dmat, p->gap_open,
+    k_sw_carry<<<blocks3, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, dmat,
+                                               p->gap_open,
                                                p->gap_extend, p->ani_min_pct, p->cov_min_pct,
                                                (stripe3_cell *)scratch, sstride, flags + 8, res, d_out, flags,
                                                (unsigned long long *)d_cells);

@@ -1,0 +1,201 @@
+"""Serving loop: query batches against a device-resident database index, with
+continuous batching.
+
+The database (residue codes, offsets and its sequence x k-mer matrix in CSR + CSC) is
+built once and stays on the device.  Requests (a batch of 1..4096 query proteins each)
+enter a queue; `slots` worker threads, each with its own CUDA stream and library
+context, take the next request as soon as they are free and the device has room for
+it (admission by free device memory), so requests that arrive while others run are
+admitted as slots and memory free up, and their kernels overlap on the GPU.  Each
+request runs the hot path in serving form: encode -> query k-mer matrix -> query x
+database candidates -> alignment -> filter, and
+returns the edges (query index, database index, ident, cols, score, ANI).  Every
+numeric step is a library kernel; this module only schedules.
+"""
+import concurrent.futures
+import ctypes
+import queue
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import pastis as P
+
+
+class Request:
+    def __init__(self, ascii_host: np.ndarray, offsets_host: np.ndarray, rid: int):
+        self.ascii = ascii_host
+        self.offsets = offsets_host
+        self.rid = rid
+        self.n = int(offsets_host.shape[0] - 1)
+        self.t_submit = time.perf_counter()
+        self.t_start = None
+        self.t_done = None
+        self.future = concurrent.futures.Future()
+
+
+def _kmat_c(A):
+    return A.c()
+
+
+class Server:
+    """Query batches against a resident database."""
+
+    def __init__(self, db_ascii: np.ndarray, db_offsets: np.ndarray, params: P.Params, device: int = 0,
+                 slots: int = 4, reserve_bytes: int = 8 << 30):
+        if params.m_subs != 0:
+            raise ValueError("the serving form takes exact k-mers (m_subs = 0)")
+        self.params = params
+        self.device = torch.device("cuda", device)
+        self.reserve = reserve_bytes
+        torch.cuda.set_device(self.device)
+        build_stream = torch.cuda.Stream(self.device)
+        with torch.cuda.stream(build_stream):
+            ctx = P.Context(device, build_stream)
+            a = torch.from_numpy(np.ascontiguousarray(db_ascii)).to(self.device)
+            self.db_offsets = torch.from_numpy(np.ascontiguousarray(db_offsets)).to(self.device)
+            self.db_codes = P.encode(ctx, a)
+            self.DB = P.build_kmers(ctx, self.db_codes, self.db_offsets, params.k)
+            build_stream.synchronize()
+            ctx.close()
+        self.n_db = int(db_offsets.shape[0] - 1)
+        self.q = queue.Queue()
+        self.mem_lock = threading.Lock()
+        self.in_flight_bytes = 0
+        self.stop = False
+        self.done = []
+        self.workers = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(slots)]
+        for w in self.workers:
+            w.start()
+
+    # -- public --------------------------------------------------------------------
+    def submit(self, ascii_host: np.ndarray, offsets_host: np.ndarray, rid: int = 0) -> Request:
+        r = Request(ascii_host, offsets_host, rid)
+        self.q.put(r)
+        return r
+
+    def close(self):
+        self.stop = True
+        for _ in self.workers:
+            self.q.put(None)
+        for w in self.workers:
+            w.join(timeout=60)
+
+    def latency_stats(self):
+        lat = np.array([r.t_done - r.t_submit for r in self.done])
+        nq = sum(r.n for r in self.done)
+        if lat.size == 0:
+            return {}
+        span = max(r.t_done for r in self.done) - min(r.t_submit for r in self.done)
+        return {"requests": int(lat.size), "queries": int(nq), "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "queries_per_s": nq / span if span > 0 else 0.0}
+
+    # -- the work of one request ------------------------------------------------------
+    def estimate_bytes(self, r: Request) -> int:
+        residues = int(r.offsets[-1])
+        # query A and its sort buffers, candidates (records, alignments), alignment scratch
+        return residues * 48 + r.n * 4096 * 60 + (64 << 20)
+
+    def process(self, ctx: P.Context, r: Request) -> np.ndarray:
+        dev = self.device
+        a = torch.from_numpy(np.ascontiguousarray(r.ascii)).to(dev, non_blocking=True)
+        o = torch.from_numpy(np.ascontiguousarray(r.offsets)).to(dev, non_blocking=True)
+        codes = P.encode(ctx, a)
+        Q = P.build_kmers(ctx, codes, o, self.params.k)
+        cands = query_overlap(ctx, Q, self.DB, self.params)
+        alns = align_pairs_qt(ctx, codes, o, self.db_codes, self.db_offsets, cands, self.params)
+        edges = filter_edges_qt(ctx, o, self.db_offsets, cands, alns, self.params)
+        return P.to_records(edges, P.EDGE_DTYPE)
+
+    def _worker(self, slot: int):
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(self.device)
+        with torch.cuda.stream(stream):
+            ctx = P.Context(self.device.index or 0, stream)
+            while True:
+                r = self.q.get()
+                if r is None:
+                    break
+                need = self.estimate_bytes(r)
+                waited = 0.0
+                while True:               # admission by free device memory (bounded wait)
+                    with self.mem_lock:
+                        free, _ = torch.cuda.mem_get_info(self.device)
+                        if free - self.in_flight_bytes - self.reserve >= need or self.in_flight_bytes == 0 \
+                                or waited > 30.0:
+                            self.in_flight_bytes += need
+                            break
+                    time.sleep(0.002)
+                    waited += 0.002
+                r.t_start = time.perf_counter()
+                try:
+                    res = self.process(ctx, r)
+                    stream.synchronize()
+                    r.t_done = time.perf_counter()
+                    self.done.append(r)
+                    r.future.set_result(res)
+                except Exception as exc:       # the request fails, the server keeps going
+                    r.t_done = time.perf_counter()
+                    r.future.set_exception(exc)
+                finally:
+                    with self.mem_lock:
+                        self.in_flight_bytes -= need
+            ctx.close()
+
+
+# ---- bindings of the serving-form entry points ---------------------------------------
+def _sigs():
+    L = P.lib()
+    if not getattr(L, "_serve_sigs", False):
+        Pp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.pastis_query_overlap.argtypes = [Pp, ctypes.POINTER(P.c_kmat), ctypes.POINTER(P.c_kmat),
+                                           ctypes.POINTER(P.c_params), Pp, i64, ctypes.POINTER(i64)]
+        L.pastis_query_overlap.restype = i32
+        L.pastis_align_pairs_qt.argtypes = [Pp, Pp, Pp, i32, Pp, Pp, i32, Pp, i64, ctypes.POINTER(P.c_params), Pp, Pp]
+        L.pastis_align_pairs_qt.restype = i32
+        L.pastis_filter_edges_qt.argtypes = [Pp, Pp, i32, Pp, i32, Pp, Pp, i64, ctypes.POINTER(P.c_params), Pp, i64,
+                                             ctypes.POINTER(i64)]
+        L.pastis_filter_edges_qt.restype = i32
+        L._serve_sigs = True
+    return L
+
+
+def query_overlap(ctx, Q, DB, params) -> torch.Tensor:
+    L = _sigs()
+    p, qm, dm = params.c(), Q.c(), DB.c()
+    nout = ctypes.c_int64()
+    st = L.pastis_query_overlap(ctx.h, ctypes.byref(qm), ctypes.byref(dm), ctypes.byref(p), None, 0,
+                                ctypes.byref(nout))
+    if st not in (0, P.ERR_CAPACITY):
+        P._check("pastis_query_overlap", st)
+    out = torch.empty((max(nout.value, 1), P.REC_BYTES), dtype=torch.uint8, device=Q.row_ptr.device)
+    if nout.value > 0:
+        P._check("pastis_query_overlap", L.pastis_query_overlap(ctx.h, ctypes.byref(qm), ctypes.byref(dm),
+                                                                ctypes.byref(p), P._ptr(out), nout.value,
+                                                                ctypes.byref(nout)))
+    return out[:nout.value]
+
+
+def align_pairs_qt(ctx, qcodes, qoff, tcodes, toff, pairs, params, cells=None) -> torch.Tensor:
+    L = _sigs()
+    n = pairs.shape[0]
+    out = torch.empty((max(n, 1), P.REC_BYTES), dtype=torch.uint8, device=qcodes.device)
+    p = params.c()
+    P._check("pastis_align_pairs_qt", L.pastis_align_pairs_qt(
+        ctx.h, P._ptr(qcodes), P._ptr(qoff), qoff.numel() - 1, P._ptr(tcodes), P._ptr(toff), toff.numel() - 1,
+        P._ptr(pairs), n, ctypes.byref(p), P._ptr(out), P._ptr(cells)))
+    return out[:n]
+
+
+def filter_edges_qt(ctx, qoff, toff, pairs, alns, params) -> torch.Tensor:
+    L = _sigs()
+    n = pairs.shape[0]
+    p = params.c()
+    nout = ctypes.c_int64()
+    out = torch.empty((max(n, 1), P.REC_BYTES), dtype=torch.uint8, device=qoff.device)
+    P._check("pastis_filter_edges_qt", L.pastis_filter_edges_qt(
+        ctx.h, P._ptr(qoff), qoff.numel() - 1, P._ptr(toff), toff.numel() - 1, P._ptr(pairs), P._ptr(alns), n,
+        ctypes.byref(p), P._ptr(out), max(n, 1), ctypes.byref(nout)))
+    return out[:nout.value]
