@@ -195,7 +195,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------
-# learned prefilter vs plain (SURVEY next row f2)
+# learned prefilter vs plain
 # ---------------------------------------------------------------------------------
 def run_prefilter(args):
     """Trains the MLP on pass/fail labels of the exact path over one row block of the
@@ -306,7 +306,7 @@ def run_prefilter(args):
 
 
 # ---------------------------------------------------------------------------------
-# serving: query batches against a resident database (SURVEY next row f3)
+# serving: query batches against a resident database
 # ---------------------------------------------------------------------------------
 def run_serve(args):
     """Database = the workload's protein set (exact k-mers, resident on the device).

@@ -254,7 +254,7 @@ pastis_status pastis_filter_edges(pastis_ctx *ctx, const int64_t *d_offsets, int
                                   int64_t n_pairs, const pastis_params *params,
                                   pastis_edge *d_out, int64_t capacity, int64_t *n_out);
 
-/* ---- learned prefilter (SURVEY next row; no counterpart in the paper's method) ----
+/* ---- learned prefilter (an extension; no counterpart in the paper's method) ----
  * A 16 -> 256 -> 256 -> 1 MLP over per-pair features predicts whether a candidate's
  * alignment will pass the filter, so that predicted failures skip alignment.  It is
  * the learned analogue of the paper's common-k-mer threshold (Sec. VI, which trades
