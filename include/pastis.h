@@ -295,6 +295,41 @@ pastis_status pastis_filter_edges_qt(pastis_ctx *ctx, const int64_t *d_qoffsets,
                                      const pastis_aln *d_alns, int64_t n_pairs, const pastis_params *params,
                                      pastis_edge *d_out, int64_t capacity, int64_t *n_out);
 
+/* ---- a10 without allocation ---------------------------------------------------------
+ * The paper has no counterpart of this call: it is pastis_filter_edges (same keep rule
+ * of Sec. IV-F, same edges of Sec. VI-B, same pair order, bit-identical output) for
+ * callers that may not allocate device memory -- a worker whose device memory is all
+ * committed (a serving slot admitted against a fixed memory budget), or one that must
+ * not call cudaFree, which waits for the whole device and so stalls other streams.
+ * It takes no context (creating one allocates its workspace) and neither calls
+ * cudaMalloc/cudaFree nor any library that allocates: its scratch is one fixed device
+ * array of PASTIS_FILTER_STATIC_SCRATCH_BYTES inside this library (a kept count and an
+ * offset per tile of 1,024 pairs, an error word, the total).
+ *
+ * stream      a cudaStream_t (NULL: the legacy default stream) of the current device;
+ *             every d_* pointer is device memory of that device, owned by the caller.
+ * d_offsets   n_seqs + 1 offsets of the sequences that pair indices i, j refer to.
+ * d_pairs, d_alns   n_pairs candidates and their alignments (pastis_align_pairs order).
+ * d_out, capacity   room for edges; *n_out receives the number of edges.
+ * Limits and errors: n_pairs > PASTIS_FILTER_STATIC_MAX_PAIRS returns
+ * PASTIS_ERR_UNSUPPORTED before any work; a pair index outside [0, n_seqs) returns
+ * PASTIS_ERR_INVALID_ARG; too small a capacity returns PASTIS_ERR_CAPACITY with the
+ * needed count in *n_out and nothing written.  Nothing the caller passes has to start
+ * at zero; the call clears its own error word first.
+ * Set-up: the first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current) and keeps it; make that first call
+ * before any stream capture begins.  Every call after it does no set-up.
+ * Concurrency: all calls on one device share the one scratch array, so calls that
+ * overlap in time (from several threads, or on several streams) race and corrupt each
+ * other's result; the caller runs them one at a time per device.
+ * Synchronises the stream twice (to read the total, and at the end).                   */
+#define PASTIS_FILTER_STATIC_MAX_PAIRS 4194304
+#define PASTIS_FILTER_STATIC_SCRATCH_BYTES 33024
+pastis_status pastis_filter_edges_static(void *stream, const int64_t *d_offsets, int32_t n_seqs,
+                                         const pastis_cand *d_pairs, const pastis_aln *d_alns,
+                                         int64_t n_pairs, const pastis_params *params,
+                                         pastis_edge *d_out, int64_t capacity, int64_t *n_out);
+
 #ifdef __cplusplus
 }
 #endif

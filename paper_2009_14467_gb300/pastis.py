@@ -299,6 +299,32 @@ def filter_edges(ctx: Context, offsets: torch.Tensor, pairs: torch.Tensor, alns:
     return out[:nout.value]
 
 
+FILTER_STATIC_MAX_PAIRS = 4194304      # PASTIS_FILTER_STATIC_MAX_PAIRS
+
+
+def filter_edges_static(stream: torch.cuda.Stream, offsets: torch.Tensor, pairs: torch.Tensor, alns: torch.Tensor,
+                        params: Params, out: torch.Tensor) -> int:
+    """pastis_filter_edges_static: the filter into the caller's `out` (uint8 [cap, 20])
+    with no allocation inside the call; returns the number of edges written.  Calls on
+    one device must not overlap in time (they share one scratch array)."""
+    L = lib()
+    if not getattr(L, "_static_sigs", False):
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.pastis_filter_edges_static.argtypes = [P, P, i32, P, P, i64, ctypes.POINTER(c_params), P, i64,
+                                                 ctypes.POINTER(i64)]
+        L.pastis_filter_edges_static.restype = i32
+        L._static_sigs = True
+    n = pairs.shape[0]
+    if n > FILTER_STATIC_MAX_PAIRS:
+        raise PastisError("pastis_filter_edges_static", 7, f"n_pairs {n} exceeds {FILTER_STATIC_MAX_PAIRS}")
+    p = params.c()
+    nout = ctypes.c_int64()
+    _check("pastis_filter_edges_static", L.pastis_filter_edges_static(
+        ctypes.c_void_p(stream.cuda_stream), _ptr(offsets), offsets.numel() - 1, _ptr(pairs), _ptr(alns), n,
+        ctypes.byref(p), _ptr(out), out.shape[0], ctypes.byref(nout)))
+    return nout.value
+
+
 def to_records(t: torch.Tensor, dtype: np.dtype) -> np.ndarray:
     """Device record bytes -> numpy structured array (host copy)."""
     a = t.detach().to("cpu").contiguous().numpy()
