@@ -7,29 +7,33 @@
 // alignment a traceback from the end selects when it prefers the diagonal, then F,
 // then E, and a gap open over an extension (its begin, identities, columns).
 //
-// Pass 1 (the whole matrix, every pair): score and end only.  A warp owns a pair;
-//   lane l owns 16 consecutive query rows and at step s computes column j = s - l,
-//   taking the H/F of the row above from lane l-1 (__shfl_up_sync).  Scores come from
-//   a query profile in shared memory (int16, [target residue][query row]) shared by
-//   every warp of the CTA: the CTA works through a run of pairs with the same query
-//   (candidate lists are grouped by i).  The end is tracked with one key per cell,
-//   key = H * 2^16 + (65535 - i): the largest key is the largest H on the smallest
-//   row, and a lane keeps the first column where its largest key appears, which is
-//   the row-major first maximum.  Queries longer than 512 rows go in stripes whose
-//   last row is handed on through a per-warp buffer.
-// Pass 2 (right after pass 1, same warp; a region around the path): an anchored DP
-//   over the reversed prefixes from the end (ei, ej).  A suffix of the traced path
-//   starting on row i scores S minus the forward value before it, which is at most
-//   the largest H pass 1 met on row i-1's 16-row block; cells below that threshold
-//   die, the path's suffixes all survive, and the cells reaching S bound the begin.
-//   Their extent gives a rectangle that contains the whole traced path.
+// Pass 1 (the whole matrix, every pair): score and end only.  A warp takes two pairs
+//   that share the query (candidate lists are grouped by i; within a run of pairs of
+//   one query they are taken in order of target length, so the two matrices match)
+//   and holds them in the two 16-bit halves of each register, so one 16x2 maximum or
+//   one 32-bit add advances both.  Lane l owns up to 16 consecutive query rows and at
+//   step s computes column j = s - l, taking H/F of the row above from lane l-1
+//   (__shfl_up_sync).  Scores come from a biased query profile in shared memory
+//   (int16, [target residue][query row]) shared by every warp of the CTA.  Each row
+//   keeps a key (H << 16 | 65535 - j) of its first maximum; the end is the first row
+//   with the best score, at that row's first maximum: the row-major first maximum.
+//   Queries longer than one stripe of 32 * 16 rows go in stripes whose last row is
+//   handed on through a per-warp buffer.
+// Pass 2 (right after pass 1, same warp, one pair at a time; a band around the path):
+//   an anchored DP over the reversed prefixes from the end (ei, ej), one lane per cell
+//   of an antidiagonal.  A suffix of the traced path starting on row i scores S minus
+//   the forward value before it, which is at most the largest H pass 1 met on row
+//   i-1's pair of rows; cells below that threshold die, the path's suffixes all
+//   survive, and the cells reaching S bound the begin.  Their extent gives a rectangle
+//   that contains the whole traced path.
 // Pass 3 (that rectangle): the DP again with zero boundaries; each state carries its
 //   begin cell and (identities << 16 | matched columns) along the predecessor a
 //   traceback would take.  Inside a rectangle holding the path, the path's cells keep
 //   their values and every choice along it is the same, so the carry at the end cell
 //   is the traceback's.  cols = span_q + span_t - matched.
-// Scores that could reach 2^15 (11 * min length >= 32768 with BLOSUM62) take pass 3
-// over the whole matrix with the end tracked there instead (all int32 either way).
+// Pairs whose scores could reach SCORE_MAX (max score * shorter length), gap costs
+// with o + e > GAP_MAX, and queries longer than the shared-memory profile take pass 3
+// over the whole matrix with the end tracked there instead (int32).
 #include <algorithm>
 
 #include "internal.cuh"
@@ -39,8 +43,7 @@ namespace {
 constexpr int NEG = -1000000000;
 constexpr int SW_THREADS = 256;
 constexpr int SW_WARPS = SW_THREADS / 32;
-constexpr int LR = 16;                     // query rows per lane in pass 1
-constexpr int STRIPE1 = 32 * LR;           // rows per stripe in pass 1
+constexpr int STRIPE1 = 512;               // rows per stripe in pass 1 at 16 rows per lane
 constexpr int PAD_SCORE = -30000;
 constexpr int SEG_MAX = 64;                // pairs per scheduling segment
 
@@ -67,195 +70,25 @@ __global__ void k_seg_starts(const uint32_t *flags, const uint32_t *off, int64_t
 }
 
 // ---------------------------------------------------------------------------------
-// pass 1
+// pass 1: two pairs per warp, one in each 16-bit half of every register
 // ---------------------------------------------------------------------------------
-struct stripe1_cell { int32_t h, f; };
+// Values are stored biased, v = x + BIAS per half.  Every state of the recurrence
+// stays in [0, 32767] when o + e <= GAP_MAX, the scores lie in [-64, 63] and no score
+// can reach SCORE_MAX: H >= 0, E and F >= -o (a gap is at least as good as opening it
+// from H >= 0), and the largest value is the best score plus one substitution.  So
+// plain 32-bit adds and subtracts never carry between the halves, and the signed
+// 16x2 maximum compares both pairs at once.
+constexpr int BIAS = 64;
+constexpr int GAP_MAX = 60;
+constexpr int SCORE_MAX = 32000;
+constexpr uint32_t P2 = 0x00010001u;
+constexpr int NRES = PASTIS_NSYM + 1;      // profile rows: the residues, then the pad residue
+constexpr int PAD_RES = PASTIS_NSYM;       // stands for target columns past the shorter target
 
-__device__ __forceinline__ int sx_lo(uint32_t w) { return (int)(int16_t)(w & 0xFFFF); }
-__device__ __forceinline__ int sx_hi(uint32_t w) { return (int)w >> 16; }
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) { return __vmaxs2(a, b); }
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) { return __byte_perm(a, b, sel); }
 
-// LR query rows per lane (even, 2..16, from the query length, so that the padding past
-// the query stays small); a stripe is 32 * LR rows.  bm4[g] receives, for every pair of
-// rows, the largest H of the lane block that holds it (an upper bound per row).
-template <int LR>
-__device__ void score_warp(const int16_t *__restrict__ prof, int prow, const uint8_t *__restrict__ t, int m,
-                           int n, int o, int e, stripe1_cell *scratch, int sstride, int16_t *bm4, int *best_h,
-                           int *best_i, int *best_j) {
-    constexpr int STRIPE = 32 * LR;
-    const int lane = threadIdx.x & 31;
-    int bestkey = 65535, bestj = 0;
-    const int nstripes = (m + STRIPE - 1) / STRIPE;
-    for (int stripe = 0; stripe < nstripes; ++stripe) {
-        const int row0 = stripe * STRIPE + lane * LR;
-        // key addend: 65535 - i on real rows; rows past the query get INT_MIN, so
-        // their keys (H * 2^16 + INT_MIN < 0) never win
-        int H[LR], E[LR], ck[LR];
-#pragma unroll
-        for (int r = 0; r < LR; ++r) {
-            const int i = row0 + r;
-            H[r] = 0;
-            E[r] = NEG;
-            ck[r] = i < m ? 65535 - i : (int)0x80000000;
-        }
-        int dtop = 0;                                  // H(row0-1, j-1)
-        int out_h = 0, out_f = NEG, out_t = 0;
-        const stripe1_cell *in_buf = scratch + (size_t)(stripe & 1) * sstride;
-        stripe1_cell *out_buf = scratch + (size_t)((stripe + 1) & 1) * sstride;
-        const bool last = stripe + 1 == nstripes;
-        const int16_t *prow0 = prof + row0;
-        int blockkey = 0;                              // largest key of this lane's rows
-        for (int s = 0; s < n + 31; ++s) {
-            const int j = s - lane;
-            int up_h = __shfl_up_sync(0xffffffffu, out_h, 1);
-            int up_f = __shfl_up_sync(0xffffffffu, out_f, 1);
-            int tj = __shfl_up_sync(0xffffffffu, out_t, 1);
-            if (lane == 0 && j < n) {
-                tj = t[j];
-                if (stripe == 0) { up_h = 0; up_f = NEG; }
-                else { const stripe1_cell c = in_buf[j]; up_h = c.h; up_f = c.f; }
-            }
-            if (j >= 0 && j < n) {
-                uint32_t ws[LR / 2];
-                if (LR % 8 == 0) {
-                    const uint4 *pv = reinterpret_cast<const uint4 *>(prow0 + tj * prow);
-#pragma unroll
-                    for (int k = 0; k < LR / 8; ++k) {
-                        const uint4 v = pv[k];
-                        ws[4 * k] = v.x; ws[4 * k + 1] = v.y; ws[4 * k + 2] = v.z; ws[4 * k + 3] = v.w;
-                    }
-                } else if (LR % 4 == 0) {
-                    const uint2 *pv = reinterpret_cast<const uint2 *>(prow0 + tj * prow);
-#pragma unroll
-                    for (int k = 0; k < LR / 4; ++k) {
-                        const uint2 v = pv[k];
-                        ws[2 * k] = v.x; ws[2 * k + 1] = v.y;
-                    }
-                } else {
-                    const uint32_t *pv = reinterpret_cast<const uint32_t *>(prow0 + tj * prow);
-#pragma unroll
-                    for (int k = 0; k < LR / 2; ++k) ws[k] = pv[k];
-                }
-                int sk = 0;
-                int hprev = dtop;                      // H(i-1, j-1) for the row being done
-                int ha = up_h, f = up_f;               // H(i-1, j), F(i-1, j)
-#pragma unroll
-                for (int r = 0; r < LR; ++r) {
-                    const int sc = (r & 1) ? sx_hi(ws[r >> 1]) : sx_lo(ws[r >> 1]);
-                    const int d = hprev + sc;
-                    const int ev = max(H[r] - o, E[r] - e);
-                    f = max(ha - o, f - e);
-                    const int h = max(__vimax3_s32(d, ev, f), 0);
-                    hprev = H[r];
-                    H[r] = h;
-                    E[r] = ev;
-                    ha = h;
-                    sk = max(sk, h * 65536 + ck[r]);
-                }
-                if (sk > bestkey) { bestkey = sk; bestj = j; }
-                blockkey = max(blockkey, sk);
-                dtop = up_h;
-                out_h = ha; out_f = f; out_t = tj;
-                if (lane == 31 && !last) out_buf[j] = stripe1_cell{ha, f};
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < LR / 2; ++g) bm4[(row0 >> 1) + g] = (int16_t)(blockkey >> 16);
-        __syncwarp();
-    }
-    // row-major first maximum across the warp: the largest key (ties cannot cross lanes)
-    bestkey = max(bestkey, 65535);
-    const int top = __reduce_max_sync(0xffffffffu, bestkey);
-    const unsigned who = __ballot_sync(0xffffffffu, bestkey == top);
-    *best_h = top >> 16;
-    *best_i = 65535 - (top & 0xFFFF);
-    *best_j = __shfl_sync(0xffffffffu, bestj, __ffs(who) - 1);
-}
-
-// ---------------------------------------------------------------------------------
-// pass 2: bounding rectangle of the traced path, by an anchored DP over the reversed
-// prefixes in which cells below 0 die
-// ---------------------------------------------------------------------------------
-constexpr int WIN = 64;           // cells of one antidiagonal kept in shared memory
-
-// The suffix of the traced path that starts on forward row i scores S minus the
-// forward value of the path state before it, which sits on row i-1; that value is at
-// most bm4[(i-1)/2], the largest H pass 1 saw on those rows.  When the split falls
-// inside a gap run, the reverse DP charges the suffix's part of the run an open
-// instead of an extension, so its reverse value can be lower by o - e.  A reverse cell
-// whose first row is i therefore dies below S - bm4[(i-1)/2] - (o - e) (bm = 0 above
-// row 0); every suffix of the path meets the bound, so the path survives, and the
-// cells reaching S bound its begin.  Three antidiagonals of H, E, F live in a circular
-// window of WIN cells per array; a live band wider than that returns false and the
-// caller falls back to the whole up-left rectangle.
-__device__ bool bound_warp(const uint8_t *q, int A, const uint8_t *t, int B, const int8_t *s_mat8, int o, int e,
-                           int S, int ei, const int16_t *bm4, int32_t *win, int *amax_out, int *bmax_out) {
-    // q[-a], t[-b] for a, b >= 0 walk backwards from the end cell (ei, ej).  The cells of
-    // antidiagonal d are those next to the live cells of d-1 (up, left) or of d-2
-    // (diagonal).
-    const int lane = threadIdx.x & 31;
-    const int slack = max(o - e, 0);
-    int32_t *WH = win, *WE = win + 3 * WIN, *WF = win + 6 * WIN;
-    int lo[3], hi[3];
-    if (lane == 0) { WH[0] = 0; WE[0] = NEG; WF[0] = NEG; }
-    __syncwarp();
-    lo[0] = 0; hi[0] = 0; lo[1] = 1; hi[1] = 0; lo[2] = 1; hi[2] = 0;
-    int l1lo = 0, l1hi = 0;          // live range of d-1
-    int l2lo = 1, l2hi = 0;          // live range of d-2 (empty)
-    int amax = 0, bmax = 0;
-    for (int d = 1; d <= A + B; ++d) {
-        int clo = 0x7FFFFFFF, chi = -1;
-        if (l1lo <= l1hi) { clo = l1lo; chi = l1hi + 1; }
-        if (l2lo <= l2hi) { clo = min(clo, l2lo + 1); chi = max(chi, l2hi + 1); }
-        if (chi < 0) break;                               // nothing live on d-1 or d-2
-        clo = max(max(clo, d - B), 0);
-        chi = min(min(chi, A), d);
-        if (chi - clo + 1 > WIN) return false;
-        const int sc = d % 3, s1 = (d + 2) % 3, s2 = (d + 1) % 3;
-        int my_lo = 0x7FFFFFFF, my_hi = -1, my_a = 0, my_b = 0;
-        if (clo <= chi) {
-            int32_t *Hd = WH + sc * WIN, *Ed = WE + sc * WIN, *Fd = WF + sc * WIN;
-            const int32_t *H1 = WH + s1 * WIN, *E1 = WE + s1 * WIN, *F1 = WF + s1 * WIN, *H2 = WH + s2 * WIN;
-            const int lo1 = lo[s1], hi1 = hi[s1], lo2 = lo[s2], hi2 = hi[s2];
-            for (int a = clo + lane; a <= chi; a += 32) {
-                const int b = d - a;
-                const int x = a & (WIN - 1), x1 = (a - 1) & (WIN - 1);
-                int ev = NEG, fv = NEG, dv = NEG;
-                if (b >= 1 && a >= lo1 && a <= hi1) ev = max(H1[x] - o, E1[x] - e);
-                if (a >= 1 && a - 1 >= lo1 && a - 1 <= hi1) fv = max(H1[x1] - o, F1[x1] - e);
-                if (a >= 1 && b >= 1 && a - 1 >= lo2 && a - 1 <= hi2) {
-                    const int hd = H2[x1];
-                    if (hd != NEG) dv = hd + s_mat8[q[-(a - 1)] * PASTIS_NSYM + t[-(b - 1)]];
-                }
-                if (ev < NEG) ev = NEG;
-                if (fv < NEG) fv = NEG;
-                int h = max(max(dv, fv), ev);
-                const int i = ei - a + 1;                 // first forward row of the suffix
-                const int thr = S - (i >= 1 ? (int)bm4[(i - 1) >> 1] : 0) - slack;
-                if (h < thr) { h = NEG; ev = NEG; fv = NEG; }
-                Hd[x] = h; Ed[x] = ev; Fd[x] = fv;
-                if (h != NEG) {
-                    my_lo = min(my_lo, a);
-                    my_hi = max(my_hi, a);
-                    if (h == S) { my_a = max(my_a, a); my_b = max(my_b, b); }
-                }
-            }
-            lo[sc] = clo; hi[sc] = chi;
-        } else {
-            lo[sc] = 1; hi[sc] = 0;
-        }
-        my_lo = __reduce_min_sync(0xffffffffu, my_lo);
-        my_hi = __reduce_max_sync(0xffffffffu, my_hi);
-        my_a = __reduce_max_sync(0xffffffffu, my_a);
-        my_b = __reduce_max_sync(0xffffffffu, my_b);
-        amax = max(amax, my_a);
-        bmax = max(bmax, my_b);
-        l2lo = l1lo; l2hi = l1hi;
-        if (my_hi >= 0) { l1lo = my_lo; l1hi = my_hi; } else { l1lo = 1; l1hi = 0; }
-    }
-    *amax_out = amax;
-    *bmax_out = bmax;
-    return true;
-}
+struct end_cell { int h, i, j; };
 
 // Rows per lane: as few stripes as 16 rows per lane allow, then the smallest even row
 // count that covers the query in that many stripes.
@@ -265,25 +98,220 @@ __device__ __forceinline__ int rows_per_lane(int m) {
     return min(16, max(2, (per + 1) & ~1));
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *qcodes, const int64_t *qoffsets,
+// One column of a lane's LR rows for both pairs.  prof rows are biased scores
+// (score + BIAS, 0 for the pad residue and for rows past the query).  The key of a row
+// keeps (Ho << 16 | 65535 - j) of its best column: the largest Ho, then the first
+// column, i.e. the first maximum of that row.
+template <int LR>
+__device__ __forceinline__ void column2(const int16_t *__restrict__ pa, const int16_t *__restrict__ pb,
+                                        uint32_t (&Ho)[LR], uint32_t (&E)[LR], uint32_t (&kA)[LR],
+                                        uint32_t (&kB)[LR], uint32_t hdiag, uint32_t &f, uint32_t &hup, uint32_t jt,
+                                        uint32_t OP, uint32_t EP, uint32_t KD) {
+    constexpr uint32_t Z = (uint32_t)BIAS * P2;
+    uint32_t wa[LR / 2], wb[LR / 2];
+    if (LR % 8 == 0) {
+        const uint4 *va = reinterpret_cast<const uint4 *>(pa), *vb = reinterpret_cast<const uint4 *>(pb);
+#pragma unroll
+        for (int k = 0; k < LR / 8; ++k) {
+            const uint4 x = va[k], y = vb[k];
+            wa[4 * k] = x.x; wa[4 * k + 1] = x.y; wa[4 * k + 2] = x.z; wa[4 * k + 3] = x.w;
+            wb[4 * k] = y.x; wb[4 * k + 1] = y.y; wb[4 * k + 2] = y.z; wb[4 * k + 3] = y.w;
+        }
+    } else if (LR % 4 == 0) {
+        const uint2 *va = reinterpret_cast<const uint2 *>(pa), *vb = reinterpret_cast<const uint2 *>(pb);
+#pragma unroll
+        for (int k = 0; k < LR / 4; ++k) {
+            const uint2 x = va[k], y = vb[k];
+            wa[2 * k] = x.x; wa[2 * k + 1] = x.y;
+            wb[2 * k] = y.x; wb[2 * k + 1] = y.y;
+        }
+    } else {
+        const uint32_t *va = reinterpret_cast<const uint32_t *>(pa), *vb = reinterpret_cast<const uint32_t *>(pb);
+#pragma unroll
+        for (int k = 0; k < LR / 2; ++k) { wa[k] = va[k]; wb[k] = vb[k]; }
+    }
+#pragma unroll
+    for (int r = 0; r < LR; ++r) {
+        const uint32_t s = prmt(wa[r >> 1], wb[r >> 1], (r & 1) ? 0x7632u : 0x5410u);
+        const uint32_t d = hdiag + s + KD;                 // H(i-1, j-1) + score
+        E[r] = vmax2(Ho[r], E[r] - EP);                    // E(i, j) from H(i, j-1) - o and E(i, j-1)
+        f = vmax2(hup, f - EP);                            // F(i, j) from H(i-1, j) - o and F(i-1, j)
+        const uint32_t h = vmax2(vmax2(d, E[r]), vmax2(f, Z));
+        hdiag = Ho[r];
+        Ho[r] = h - OP;
+        hup = Ho[r];
+        kA[r] = (uint32_t)max((int)kA[r], (int)prmt(Ho[r], jt, 0x1054u));
+        kB[r] = (uint32_t)max((int)kB[r], (int)prmt(Ho[r], jt, 0x3254u));
+    }
+}
+
+// Pass 1 over the whole matrix of two pairs with the same query: pair A (target tA,
+// nA columns) in the low halves, pair B in the high halves.  Lane l owns LR
+// consecutive query rows and at step s does column j = s - l, taking the row above from
+// lane l-1; a stripe is 32 * LR rows, its last row handed on through buf.  Columns
+// past the shorter target use the pad residue, which scores -64 against every row: a
+// cell there stays below the best score of its own pair, so it never becomes the end.
+// Returns each pair's best score and its first maximum in row-major order, and
+// writes bm[g] = the largest H on rows 2g and 2g+1 (an upper bound used by pass 2).
+template <int LR>
+__device__ void score_pair(const int16_t *__restrict__ prof, int prow, const uint8_t *__restrict__ tA, int nA,
+                           const uint8_t *__restrict__ tB, int nB, int m, int o, int e, uint2 *buf, int sstride,
+                           int16_t *bmA, int16_t *bmB, end_cell *ra, end_cell *rb) {
+    constexpr int STRIPE = 32 * LR;
+    const int lane = threadIdx.x & 31;
+    const int n = max(nA, nB);
+    const uint32_t INIT = (uint32_t)(BIAS - o) * P2;       // x = -o in both halves
+    const uint32_t OP = (uint32_t)o * P2, EP = (uint32_t)e * P2;
+    const uint32_t KD = (uint32_t)(o - BIAS) * P2;         // d = Ho(i-1, j-1) + o + score: bias folded in
+    int bA = -1, iA = 0, jA = 0, bB = -1, iB = 0, jB = 0;
+    const int nstripes = (m + STRIPE - 1) / STRIPE;
+    for (int stripe = 0; stripe < nstripes; ++stripe) {
+        const int row0 = stripe * STRIPE + lane * LR;
+        uint32_t Ho[LR], E[LR], kA[LR], kB[LR];
+#pragma unroll
+        for (int r = 0; r < LR; ++r) { Ho[r] = INIT; E[r] = INIT; kA[r] = 0; kB[r] = 0; }
+        uint32_t hd = INIT;                                 // Ho(row0 - 1, j - 1)
+        uint32_t out_h = INIT, out_f = INIT, out_t = 0;
+        const uint2 *in_buf = buf + (size_t)(stripe & 1) * sstride;
+        uint2 *out_buf = buf + (size_t)((stripe + 1) & 1) * sstride;
+        const bool last = stripe + 1 == nstripes;
+        const int16_t *pr = prof + row0;
+        for (int s = 0; s < n + 31; ++s) {
+            const int j = s - lane;
+            uint32_t hu = __shfl_up_sync(0xffffffffu, out_h, 1);
+            uint32_t fu = __shfl_up_sync(0xffffffffu, out_f, 1);
+            uint32_t tt = __shfl_up_sync(0xffffffffu, out_t, 1);
+            if (lane == 0 && j < n) {
+                const uint32_t ca = j < nA ? (uint32_t)tA[j] : (uint32_t)PAD_RES;
+                const uint32_t cb = j < nB ? (uint32_t)tB[j] : (uint32_t)PAD_RES;
+                tt = ca | (cb << 16);
+                if (stripe == 0) { hu = INIT; fu = INIT; }
+                else { const uint2 c = in_buf[j]; hu = c.x; fu = c.y; }
+            }
+            if (j >= 0 && j < n) {
+                uint32_t f = fu, hup = hu;
+                column2<LR>(pr + (int)(tt & 0xFFFFu) * prow, pr + (int)(tt >> 16) * prow, Ho, E, kA, kB, hd, f, hup,
+                            65535u - (uint32_t)j, OP, EP, KD);
+                hd = hu;
+                out_h = hup; out_f = f; out_t = tt;
+                if (lane == 31 && !last) out_buf[j] = make_uint2(hup, f);
+            }
+        }
+        // this lane's rows: first maximum per pair, and the row-pair bounds
+#pragma unroll
+        for (int r = 0; r < LR; r += 2) {
+            const int xa0 = (int)(kA[r] >> 16) - BIAS + o, xa1 = (int)(kA[r + 1] >> 16) - BIAS + o;
+            const int xb0 = (int)(kB[r] >> 16) - BIAS + o, xb1 = (int)(kB[r + 1] >> 16) - BIAS + o;
+            const int i = row0 + r;
+            if (i < m) {
+                bmA[i >> 1] = (int16_t)max(xa0, xa1);
+                bmB[i >> 1] = (int16_t)max(xb0, xb1);
+                if (xa0 > bA) { bA = xa0; iA = i; jA = 65535 - (int)(kA[r] & 0xFFFFu); }
+                if (xb0 > bB) { bB = xb0; iB = i; jB = 65535 - (int)(kB[r] & 0xFFFFu); }
+            }
+            if (i + 1 < m) {
+                if (xa1 > bA) { bA = xa1; iA = i + 1; jA = 65535 - (int)(kA[r + 1] & 0xFFFFu); }
+                if (xb1 > bB) { bB = xb1; iB = i + 1; jB = 65535 - (int)(kB[r + 1] & 0xFFFFu); }
+            }
+        }
+        __syncwarp();
+    }
+    // across the warp: the largest score, then the smallest row (rows are unique per lane)
+    const int SA = __reduce_max_sync(0xffffffffu, bA), SB = __reduce_max_sync(0xffffffffu, bB);
+    const int eiA = (int)__reduce_min_sync(0xffffffffu, bA == SA ? (unsigned)iA : 0xFFFFFFFFu);
+    const int eiB = (int)__reduce_min_sync(0xffffffffu, bB == SB ? (unsigned)iB : 0xFFFFFFFFu);
+    const unsigned wa = __ballot_sync(0xffffffffu, bA == SA && iA == eiA);
+    const unsigned wb = __ballot_sync(0xffffffffu, bB == SB && iB == eiB);
+    ra->h = SA; ra->i = eiA; ra->j = __shfl_sync(0xffffffffu, jA, __ffs(wa) - 1);
+    rb->h = SB; rb->i = eiB; rb->j = __shfl_sync(0xffffffffu, jB, __ffs(wb) - 1);
+}
+
+// ---------------------------------------------------------------------------------
+// pass 2: bounding rectangle of the traced path, by an anchored DP over the reversed
+// prefixes in which cells below a bound die
+// ---------------------------------------------------------------------------------
+// The suffix of the traced path that starts on forward row i scores S minus the
+// forward value of the path state before it, which sits on row i-1; that value is at
+// most bm[(i-1)/2], the largest H pass 1 saw on that pair of rows.  When the split
+// falls inside a gap run, the reverse DP charges the suffix's part of the run an open
+// instead of an extension, so its reverse value can be lower by o - e.  A reverse cell
+// whose first row is i therefore dies below S - bm[(i-1)/2] - (o - e) (bm = 0 above
+// row 0); every suffix of the path meets the bound, so the path survives, and the
+// cells reaching S bound its begin.
+// Lane k holds cell a = base + k of the current antidiagonal (a = rows back from the
+// end, b = d - a columns back); the neighbours on the two antidiagonals before come
+// by shuffles.  A live band wider than 32 cells returns false and the caller falls
+// back to the whole up-left rectangle.
+__device__ bool bound_band(const int16_t *__restrict__ prof, int prow, const uint8_t *__restrict__ t, int o, int e,
+                           int S, int ei, int ej, const int16_t *bm, int *amax_out, int *bmax_out) {
+    const int lane = threadIdx.x & 31;
+    const int A = ei + 1, B = ej + 1;
+    const int slack = max(o - e, 0);
+    int H1 = lane == 0 ? 0 : NEG, E1 = NEG, F1 = NEG, w1 = 0;   // antidiagonal d-1 (d = 0: the end)
+    int H2 = NEG, w2 = 0;                                         // antidiagonal d-2
+    int l1lo = 0, l1hi = 0, l2lo = 1, l2hi = 0;                   // live ranges of a on d-1, d-2
+    int amax = 0, bmax = 0;
+    for (int d = 1; d <= A + B; ++d) {
+        int clo = 0x7FFFFFFF, chi = -1;
+        if (l1lo <= l1hi) { clo = l1lo; chi = l1hi + 1; }
+        if (l2lo <= l2hi) { clo = min(clo, l2lo + 1); chi = max(chi, l2hi + 1); }
+        if (chi < 0) break;                                       // nothing live on d-1 or d-2
+        clo = max(max(clo, d - B), 0);
+        chi = min(min(chi, A), d);
+        if (chi - clo + 1 > 32) return false;
+        const int a = clo + lane, b = d - a;
+        const int sa = a - w1, su = a - 1 - w1, s2 = a - 1 - w2;
+        int h1a = __shfl_sync(0xffffffffu, H1, sa & 31), e1a = __shfl_sync(0xffffffffu, E1, sa & 31);
+        int h1u = __shfl_sync(0xffffffffu, H1, su & 31), f1u = __shfl_sync(0xffffffffu, F1, su & 31);
+        int h2 = __shfl_sync(0xffffffffu, H2, s2 & 31);
+        if ((unsigned)sa > 31u) { h1a = NEG; e1a = NEG; }
+        if ((unsigned)su > 31u) { h1u = NEG; f1u = NEG; }
+        if ((unsigned)s2 > 31u) h2 = NEG;
+        int h = NEG, ev = NEG, fv = NEG;
+        if (a <= chi) {
+            if (b >= 1) ev = max(max(h1a - o, e1a - e), NEG);
+            if (a >= 1) fv = max(max(h1u - o, f1u - e), NEG);
+            int dv = NEG;
+            if (a >= 1 && b >= 1 && h2 != NEG) dv = h2 + (int)prof[(int)t[ej - (b - 1)] * prow + (ei - (a - 1))] - BIAS;
+            h = max(max(dv, ev), fv);
+            const int i = ei - a + 1;                             // first forward row of the suffix
+            const int thr = S - (i >= 1 ? (int)bm[(i - 1) >> 1] : 0) - slack;
+            if (h < thr) { h = NEG; ev = NEG; fv = NEG; }
+        }
+        const unsigned live = __ballot_sync(0xffffffffu, h != NEG);
+        if (__any_sync(0xffffffffu, h == S)) {
+            amax = max(amax, (int)__reduce_max_sync(0xffffffffu, h == S ? (unsigned)a : 0u));
+            bmax = max(bmax, (int)__reduce_max_sync(0xffffffffu, h == S ? (unsigned)b : 0u));
+        }
+        H2 = H1; w2 = w1;
+        H1 = h; E1 = ev; F1 = fv; w1 = clo;
+        l2lo = l1lo; l2hi = l1hi;
+        if (live) { l1lo = clo + __ffs(live) - 1; l1hi = clo + 31 - __clz(live); }
+        else { l1lo = 1; l1hi = 0; }
+    }
+    *amax_out = amax;
+    *bmax_out = bmax;
+    return true;
+}
+
+__global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcodes, const int64_t *qoffsets,
                                                          const uint8_t *tcodes, const int64_t *toffsets,
                                                          const pastis_cand *pairs, const int64_t *seg_start,
                                                          int64_t n_seg, const int8_t *gmat, int o, int e,
                                                          int max_s, int prow_cap, char *scratch, size_t warp_bytes,
                                                          int sstride, int *next_seg, sw_score_out *out,
                                                          unsigned long long *cells) {
-    // dynamic shared memory: profile [24][prow_cap] int16, then per warp bm4[prow_cap/2] int16
-    // and the pass-2 window [9][WIN]
+    // dynamic shared memory: profile [NRES][prow_cap] int16, then per warp two row-pair
+    // bound arrays [prow_cap / 2] int16
     extern __shared__ __align__(16) int16_t s_prof[];
     __shared__ int s_seg, s_next;
-    __shared__ int8_t s_mat8[PASTIS_NSYM * PASTIS_NSYM];
+    __shared__ uint32_t s_key[SEG_MAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * SW_WARPS + warp;
-    for (int x = threadIdx.x; x < PASTIS_NSYM * PASTIS_NSYM; x += blockDim.x) s_mat8[x] = gmat[x];
-    int16_t *bm4 = s_prof + PASTIS_NSYM * prow_cap + warp * (prow_cap / 2);
-    int32_t *win = reinterpret_cast<int32_t *>(s_prof + PASTIS_NSYM * prow_cap + SW_WARPS * (prow_cap / 2)) +
-                   warp * 9 * WIN;
-    stripe1_cell *my = reinterpret_cast<stripe1_cell *>(scratch + (size_t)gw * warp_bytes);
+    int16_t *bmA = s_prof + NRES * prow_cap + warp * prow_cap;
+    int16_t *bmB = bmA + prow_cap / 2;
+    uint2 *my = reinterpret_cast<uint2 *>(scratch + (size_t)gw * warp_bytes);
+    const bool packable = o + e <= GAP_MAX;
     unsigned long long my_cells = 0;
     for (;;) {
         if (threadIdx.x == 0) { s_seg = atomicAdd(next_seg, 1); s_next = 0; }
@@ -291,56 +319,102 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sw_score(const uint8_t *qcode
         const int64_t sg = s_seg;
         if (sg >= n_seg) break;
         const int64_t p0 = seg_start[sg], p1 = seg_start[sg + 1];
+        const int cnt = (int)(p1 - p0);
         const int qi = pairs[p0].i;
         const int64_t qo = qoffsets[qi];
         const int m = (int)(qoffsets[qi + 1] - qo);
         const int lr = rows_per_lane(m);
         const int prow = ((m + 32 * lr - 1) / (32 * lr)) * (32 * lr);
-        // query profile: prof[c][i] = M[q_i][c], PAD past the end of the query
+        // query profile: prof[c][i] = M[q_i][c] + BIAS; 0 for the pad residue and past the query
         if (prow <= prow_cap) {
-            for (int x = threadIdx.x; x < PASTIS_NSYM * prow; x += blockDim.x) {
+            for (int x = threadIdx.x; x < NRES * prow; x += blockDim.x) {
                 const int c = x / prow, i = x - c * prow;
-                s_prof[x] = (int16_t)(i < m ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] : PAD_SCORE);
+                s_prof[x] = (int16_t)((i < m && c < PASTIS_NSYM) ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] + BIAS
+                                                                 : 0);
             }
         }
+        // the segment's pairs by target length, so that the two pairs of a warp match
+        if (threadIdx.x < SEG_MAX) {
+            uint32_t key = 0xFFFFFFFFu;
+            if ((int)threadIdx.x < cnt) {
+                const int j = pairs[p0 + threadIdx.x].j;
+                key = ((uint32_t)(toffsets[j + 1] - toffsets[j]) << 6) | threadIdx.x;
+            }
+            s_key[threadIdx.x] = key;
+        }
         __syncthreads();
+        for (int k = 2; k <= SEG_MAX; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const int x = threadIdx.x, y = x ^ jj;
+                if (x < SEG_MAX && y > x) {
+                    const uint32_t u = s_key[x], v = s_key[y];
+                    if ((u > v) == ((x & k) == 0)) { s_key[x] = v; s_key[y] = u; }
+                }
+                __syncthreads();
+            }
+        }
         for (;;) {
             int pk = 0;
-            if (lane == 0) pk = atomicAdd(&s_next, 1);
+            if (lane == 0) pk = atomicAdd(&s_next, 2);
             pk = __shfl_sync(0xffffffffu, pk, 0);
-            const int64_t p = p0 + pk;
-            if (p >= p1) break;
-            const pastis_cand c = pairs[p];
-            const int64_t to = toffsets[c.j];
-            const int n = (int)(toffsets[c.j + 1] - to);
-            sw_score_out r;
-            r.score = 0; r.end_i = 0; r.end_j = 0; r.rect_i = 0; r.rect_j = 0; r.big = 0;
-            if ((int64_t)max_s * (int64_t)min(m, n) >= 32767 || prow > prow_cap) {
-                r.big = 1;                          // left to the int32 carry pass
-            } else if (m > 0 && n > 0) {
-                int bh, bi, bj;
-                const uint8_t *tp = tcodes + to;
-#define PASTIS_SW_CASE(L) \
-    case L: score_warp<L>(s_prof, prow, tp, m, n, o, e, my, sstride, bm4, &bh, &bi, &bj); break;
+            if (pk >= cnt) break;
+            int64_t pp[2];
+            int nn[2], st[2];                                     // st: 0 zero, 1 big, 2 run
+            const uint8_t *tp[2];
+            for (int u = 0; u < 2; ++u) {
+                pp[u] = pk + u < cnt ? p0 + (int64_t)(s_key[pk + u] & 63u) : -1;
+                nn[u] = 0; st[u] = 0; tp[u] = tcodes;
+                if (pp[u] < 0) continue;
+                const pastis_cand c = pairs[pp[u]];
+                const int64_t to = toffsets[c.j];
+                nn[u] = (int)(toffsets[c.j + 1] - to);
+                tp[u] = tcodes + to;
+                if (m == 0 || nn[u] == 0) st[u] = 0;
+                else if (!packable || prow > prow_cap || (int64_t)max_s * (int64_t)min(m, nn[u]) >= SCORE_MAX) st[u] = 1;
+                else st[u] = 2;
+            }
+            end_cell res[2];
+            res[0].h = res[1].h = 0;
+            if (st[0] == 2 || st[1] == 2) {
+                // both halves busy; a lone pair fills both
+                const int ua = st[0] == 2 ? 0 : 1, ub = st[1] == 2 ? 1 : 0;
+                end_cell ea, eb;
+#define PASTIS_SW_CASE(L)                                                                                       \
+    case L:                                                                                                     \
+        score_pair<L>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bmA, bmB, &ea, &eb); \
+        break;
                 switch (lr) {
                     PASTIS_SW_CASE(2) PASTIS_SW_CASE(4) PASTIS_SW_CASE(6) PASTIS_SW_CASE(8)
                     PASTIS_SW_CASE(10) PASTIS_SW_CASE(12) PASTIS_SW_CASE(14)
-                    default: score_warp<16>(s_prof, prow, tp, m, n, o, e, my, sstride, bm4, &bh, &bi, &bj); break;
+                    default:
+                        score_pair<16>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bmA, bmB,
+                                       &ea, &eb);
+                        break;
                 }
 #undef PASTIS_SW_CASE
                 __syncwarp();
-                if (bh > 0) {
-                    r.score = bh; r.end_i = bi; r.end_j = bj;
-                    int amax = 0, bmax = 0;
-                    if (bound_warp(qcodes + qo + bi, bi + 1, tp + bj, bj + 1, s_mat8, o, e, bh, bi, bm4, win,
-                                   &amax, &bmax) && amax > 0 && bmax > 0) {
-                        r.rect_i = bi + 1 - amax;
-                        r.rect_j = bj + 1 - bmax;
-                    }                                   // else: the whole up-left rectangle
-                }
-                my_cells += (unsigned long long)m * (unsigned long long)n;
+                if (st[ua] == 2) res[ua] = ea;
+                if (st[ub] == 2 && ub != ua) res[ub] = eb;
             }
-            if (lane == 0) out[p] = r;
+            for (int u = 0; u < 2; ++u) {
+                if (pp[u] < 0) continue;
+                sw_score_out r;
+                r.score = 0; r.end_i = 0; r.end_j = 0; r.rect_i = 0; r.rect_j = 0; r.big = st[u] == 1;
+                if (st[u] == 2) {
+                    if (res[u].h > 0) {
+                        r.score = res[u].h; r.end_i = res[u].i; r.end_j = res[u].j;
+                        const int16_t *bm = (u == 0 || st[0] != 2) ? bmA : bmB;
+                        int amax = 0, bmax = 0;
+                        if (bound_band(s_prof, prow, tp[u], o, e, r.score, r.end_i, r.end_j, bm, &amax, &bmax) &&
+                            amax > 0 && bmax > 0) {
+                            r.rect_i = r.end_i + 1 - amax;
+                            r.rect_j = r.end_j + 1 - bmax;
+                        }                                         // else: the whole up-left rectangle
+                    }
+                    my_cells += (unsigned long long)m * (unsigned long long)nn[u];
+                }
+                if (lane == 0) out[pp[u]] = r;
+            }
         }
         __syncthreads();
     }
@@ -684,9 +758,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     // pass 1+2: profile rows up to the longest query (in whole stripes), within shared memory
     int prow_cap = ((lmax + STRIPE1 - 1) / STRIPE1) * STRIPE1;
     if (prow_cap < STRIPE1) prow_cap = STRIPE1;
-    auto shm_for = [](int pc) {
-        return (size_t)PASTIS_NSYM * pc * 2 + (size_t)SW_WARPS * (pc / 2) * 2 + (size_t)SW_WARPS * 9 * WIN * 4;
-    };
+    auto shm_for = [](int pc) { return (size_t)NRES * pc * 2 + (size_t)SW_WARPS * pc * 2; };
     while (prow_cap > STRIPE1 && shm_for(prow_cap) + 1024 > ctx->smem_optin) prow_cap -= STRIPE1;
     const size_t shm1 = shm_for(prow_cap);
     cudaFuncSetAttribute(k_sw_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm1);
@@ -695,7 +767,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     if (per_sm < 1) per_sm = 1;
     const int blocks1 = ctx->sm_count * per_sm;
     const int sstride = lmax + 1;
-    const size_t warp_bytes = (sizeof(stripe1_cell) * 2 * (size_t)sstride + 255) & ~(size_t)255;
+    const size_t warp_bytes = (sizeof(uint2) * 2 * (size_t)sstride + 255) & ~(size_t)255;
     const size_t scr1 = warp_bytes * (size_t)blocks1 * SW_WARPS;
     const int blocks3 = ctx->sm_count * 2;
     const size_t scr3 = sizeof(stripe3_cell) * (size_t)blocks3 * SW_WARPS * 2 * sstride;

@@ -215,6 +215,33 @@ def test_sw_parity_long_and_lopsided(P, ctx):
     _cmp_alns(got, want)
 
 
+def test_sw_end_is_row_major_first_maximum(P, ctx):
+    """Two cells share the best score (51): row 6 at column 44 and row 13 at column 4,
+    both inside the first lane's block of rows.  The end must be the row-major first
+    one, (6, 44), not the one met first column by column."""
+    r = np.random.default_rng(4)
+
+    def tf(n):
+        return "".join(r.choice(list("ILV"), size=n))
+
+    p1, p2 = "WCWCW", "CWCWW"
+    t = p2 + tf(35) + p1 + tf(255)
+    strings = [t]
+    for tail in (488, 286, 120, 20):                 # 16, 10, 4 and 2 rows per lane
+        strings.append("GG" + p1 + "GG" + p2 + "G" * tail)
+    ps = synth.from_strings(strings)
+    cands = _all_pairs(ps.n)
+    got, want, _, _ = _align_both(P, ctx, ps, cands, 0)
+    _cmp_alns(got, want)
+    assert (got["score"][:ps.n - 1] == 51).all()
+    swapped = synth.from_strings(strings[1:] + [t])
+    cands = _all_pairs(swapped.n)
+    got, want, _, _ = _align_both(P, ctx, swapped, cands, 0)
+    _cmp_alns(got, want)
+    last = want[cands["j"] == swapped.n - 1]         # (query, target): the query is the row
+    assert (last["qe"] == 7).all() and (last["te"] == 45).all()
+
+
 @pytest.mark.parametrize("X", [49, 5, 0, 1000])
 def test_xd_parity_x_values(P, ctx, X):
     ps = synth.families_1k().subset(np.arange(300))
