@@ -19,7 +19,7 @@ enum ws_slot {
     WS_AS_TMP_KEY, WS_AS_TMP_VAL,
     WS_SPG_ROWWORK, WS_SPG_ROWOFF, WS_SPG_ROWCNT, WS_SPG_TMP, WS_SPG_TABLE, WS_SPG_BIN,
     WS_SPG_RESULT,
-    WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER,
+    WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER, WS_ALN_BOUND, WS_ALN_BOFF,
     WS_FILT_FLAGS, WS_FILT_SCAN,
     WS_MLP,
     WS_COUNT
@@ -106,6 +106,11 @@ pastis_status radix_sort_u32_u64(pastis_ctx *c, uint32_t *keys, uint64_t *vals,
 pastis_status exclusive_scan_u32(pastis_ctx *c, const uint32_t *in, uint32_t *out, int64_t n);
 // Exclusive scan of n int64 values into int64 offsets (n+1 entries).
 pastis_status exclusive_scan_i64(pastis_ctx *c, const int64_t *in, int64_t *out, int64_t n);
+
+// Raise the dynamic shared-memory limit of the kernels that size it per call to the
+// device's opt-in maximum (the current device; done at context creation).
+cudaError_t sw_set_smem_limit(size_t bytes);
+cudaError_t spgemm_set_smem_limit(size_t bytes);
 
 // Validates the parameters shared by the calls; returns PASTIS_OK or INVALID_ARG.
 pastis_status check_params(const pastis_params *p);

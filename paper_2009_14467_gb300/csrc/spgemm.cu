@@ -241,6 +241,19 @@ size_t table_bytes(int tsize, bool subs) {
 // The product driver.  Self mode (DB == nullptr): rows of A against A's postings,
 // columns j > i.  Query mode: rows of A (the queries) against the postings of DB,
 // every column j of DB (exact k-mers only).
+cudaError_t spgemm_set_smem_limit(size_t bytes) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_spgemm_items<true>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spgemm_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(bytes - fa.sharedSizeBytes));
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_spgemm_items<false>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spgemm_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(bytes - fa.sharedSizeBytes));
+    return e;
+}
+
 static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const pastis_kmat *DB,
                                   const pastis_params *params, int32_t row_begin, int32_t row_end, pastis_cand *d_out,
                                   int64_t capacity, int64_t *n_out) {
@@ -386,10 +399,6 @@ static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const p
             const size_t shm = table_bytes(tsize, subs);
             for (int64_t g0 = x0; g0 < x1; g0 += 65535) {
                 int64_t g1 = std::min<int64_t>(x1, g0 + 65535);
-                if (subs)
-                    cudaFuncSetAttribute(k_spgemm_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-                else
-                    cudaFuncSetAttribute(k_spgemm_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
                 prof_begin(ctx, "spgemm_items");
                 if (subs)
                     k_spgemm_items<true><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(

@@ -17,10 +17,11 @@
 //   (int16, [target residue][query row]) shared by every warp of the CTA.  Each row
 //   keeps a key (H << 16 | 65535 - j) of its first maximum; the end is the first row
 //   with the best score, at that row's first maximum: the row-major first maximum.
+//   Pass 1 also stores, per pair of query rows, the largest H it met there.
 //   Queries longer than one stripe of 32 * 16 rows go in stripes whose last row is
 //   handed on through a per-warp buffer.
-// Pass 2 (right after pass 1, same warp, one pair at a time; a band around the path):
-//   an anchored DP over the reversed prefixes from the end (ei, ej), one lane per cell
+// Pass 2 (its own kernel, one warp per pair; a band around the path): an anchored DP
+//   over the reversed prefixes from the end (ei, ej), each lane holding up to two cells
 //   of an antidiagonal.  A suffix of the traced path starting on row i scores S minus
 //   the forward value before it, which is at most the largest H pass 1 met on row
 //   i-1's pair of rows; cells below that threshold die, the path's suffixes all
@@ -45,7 +46,7 @@ constexpr int SW_THREADS = 256;
 constexpr int SW_WARPS = SW_THREADS / 32;
 constexpr int STRIPE1 = 512;               // rows per stripe in pass 1 at 16 rows per lane
 constexpr int PAD_SCORE = -30000;
-constexpr int SEG_MAX = 64;                // pairs per scheduling segment
+constexpr int SEG_MAX = 128;               // pairs per scheduling segment
 
 struct sw_score_out {                      // pass 1 result per pair
     int32_t score;
@@ -238,60 +239,131 @@ __device__ void score_pair(const int16_t *__restrict__ prof, int prow, const uin
 // whose first row is i therefore dies below S - bm[(i-1)/2] - (o - e) (bm = 0 above
 // row 0); every suffix of the path meets the bound, so the path survives, and the
 // cells reaching S bound its begin.
-// Lane k holds cell a = base + k of the current antidiagonal (a = rows back from the
-// end, b = d - a columns back); the neighbours on the two antidiagonals before come
-// by shuffles.  A live band wider than 32 cells returns false and the caller falls
-// back to the whole up-left rectangle.
-__device__ bool bound_band(const int16_t *__restrict__ prof, int prow, const uint8_t *__restrict__ t, int o, int e,
-                           int S, int ei, int ej, const int16_t *bm, int *amax_out, int *bmax_out) {
+// The band of an antidiagonal (a = rows back from the end, b = d - a columns back) is
+// held two cells per lane, index k in lane k % 32 of chunk k / 32; the neighbours on
+// the two antidiagonals before come by shuffles.  A live band wider than BAND cells
+// returns false and the caller keeps the whole up-left rectangle.
+constexpr int BAND = 64;
+
+// The value the previous antidiagonal holds at band index idx (NEG outside the band).
+// `wide` is the same on every lane.
+__device__ __forceinline__ int band_get(const int (&X)[2], int idx, bool wide) {
+    const int v0 = __shfl_sync(0xffffffffu, X[0], idx & 31);
+    int v = v0;
+    if (wide) {
+        const int v1 = __shfl_sync(0xffffffffu, X[1], idx & 31);
+        v = idx >= 32 ? v1 : v0;
+    }
+    return (unsigned)idx < (wide ? 64u : 32u) ? v : NEG;
+}
+
+__device__ bool band_walk(const uint8_t *__restrict__ q, const uint8_t *__restrict__ t, const int *s_mat, int o,
+                          int e, int S, int ei, int ej, const int16_t *__restrict__ bm, int *amax_out,
+                          int *bmax_out) {
     const int lane = threadIdx.x & 31;
     const int A = ei + 1, B = ej + 1;
     const int slack = max(o - e, 0);
-    int H1 = lane == 0 ? 0 : NEG, E1 = NEG, F1 = NEG, w1 = 0;   // antidiagonal d-1 (d = 0: the end)
-    int H2 = NEG, w2 = 0;                                         // antidiagonal d-2
-    int l1lo = 0, l1hi = 0, l2lo = 1, l2hi = 0;                   // live ranges of a on d-1, d-2
+    int H1[2] = {lane == 0 ? 0 : NEG, NEG}, E1[2] = {NEG, NEG}, F1[2] = {NEG, NEG};   // d-1 (d = 0: the end)
+    int H2[2] = {NEG, NEG};                                                          // d-2
+    int w1 = 0, W1 = 1, w2 = 0, W2 = 0;            // band start and computed width of d-1, d-2
+    int l1lo = 0, l1hi = 0, l2lo = 1, l2hi = 0;    // live ranges of a on d-1, d-2
     int amax = 0, bmax = 0;
     for (int d = 1; d <= A + B; ++d) {
         int clo = 0x7FFFFFFF, chi = -1;
         if (l1lo <= l1hi) { clo = l1lo; chi = l1hi + 1; }
         if (l2lo <= l2hi) { clo = min(clo, l2lo + 1); chi = max(chi, l2hi + 1); }
-        if (chi < 0) break;                                       // nothing live on d-1 or d-2
+        if (chi < 0) break;                        // nothing live on d-1 or d-2
         clo = max(max(clo, d - B), 0);
         chi = min(min(chi, A), d);
-        if (chi - clo + 1 > 32) return false;
-        const int a = clo + lane, b = d - a;
-        const int sa = a - w1, su = a - 1 - w1, s2 = a - 1 - w2;
-        int h1a = __shfl_sync(0xffffffffu, H1, sa & 31), e1a = __shfl_sync(0xffffffffu, E1, sa & 31);
-        int h1u = __shfl_sync(0xffffffffu, H1, su & 31), f1u = __shfl_sync(0xffffffffu, F1, su & 31);
-        int h2 = __shfl_sync(0xffffffffu, H2, s2 & 31);
-        if ((unsigned)sa > 31u) { h1a = NEG; e1a = NEG; }
-        if ((unsigned)su > 31u) { h1u = NEG; f1u = NEG; }
-        if ((unsigned)s2 > 31u) h2 = NEG;
-        int h = NEG, ev = NEG, fv = NEG;
-        if (a <= chi) {
-            if (b >= 1) ev = max(max(h1a - o, e1a - e), NEG);
-            if (a >= 1) fv = max(max(h1u - o, f1u - e), NEG);
-            int dv = NEG;
-            if (a >= 1 && b >= 1 && h2 != NEG) dv = h2 + (int)prof[(int)t[ej - (b - 1)] * prow + (ei - (a - 1))] - BIAS;
-            h = max(max(dv, ev), fv);
-            const int i = ei - a + 1;                             // first forward row of the suffix
-            const int thr = S - (i >= 1 ? (int)bm[(i - 1) >> 1] : 0) - slack;
-            if (h < thr) { h = NEG; ev = NEG; fv = NEG; }
+        const int W = max(chi - clo + 1, 0);
+        if (W > BAND) return false;
+        const bool wide = W > 32 || W1 > 32 || W2 > 32;
+        int h[2] = {NEG, NEG}, ev[2] = {NEG, NEG}, fv[2] = {NEG, NEG};
+        unsigned live[2] = {0u, 0u};
+        int ta = 0, tb = 0;                        // this lane's largest (a, b) reaching S
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c == 1 && !wide) break;
+            const int a = clo + 32 * c + lane, b = d - a;
+            const int sa = a - w1, su = a - 1 - w1, s2 = a - 1 - w2;
+            const int h1a = band_get(H1, sa, wide), e1a = band_get(E1, sa, wide);
+            const int h1u = band_get(H1, su, wide), f1u = band_get(F1, su, wide);
+            const int h2 = band_get(H2, s2, wide);
+            if (a <= chi) {
+                if (b >= 1) ev[c] = max(max(h1a - o, e1a - e), NEG);
+                if (a >= 1) fv[c] = max(max(h1u - o, f1u - e), NEG);
+                int dv = NEG;
+                if (a >= 1 && b >= 1 && h2 != NEG)
+                    dv = h2 + s_mat[(int)q[ei - (a - 1)] * PASTIS_NSYM + (int)t[ej - (b - 1)]];
+                int hh = max(max(dv, ev[c]), fv[c]);
+                const int i = ei - a + 1;          // first forward row of the suffix
+                const int thr = S - (i >= 1 ? (int)bm[(i - 1) >> 1] : 0) - slack;
+                if (hh < thr) { hh = NEG; ev[c] = NEG; fv[c] = NEG; }
+                h[c] = hh;
+                if (hh == S) { ta = a; tb = max(tb, b); }
+            }
+            live[c] = __ballot_sync(0xffffffffu, h[c] != NEG);
         }
-        const unsigned live = __ballot_sync(0xffffffffu, h != NEG);
-        if (__any_sync(0xffffffffu, h == S)) {
-            amax = max(amax, (int)__reduce_max_sync(0xffffffffu, h == S ? (unsigned)a : 0u));
-            bmax = max(bmax, (int)__reduce_max_sync(0xffffffffu, h == S ? (unsigned)b : 0u));
+        if (__any_sync(0xffffffffu, ta > 0 || tb > 0)) {
+            amax = max(amax, __reduce_max_sync(0xffffffffu, ta));
+            bmax = max(bmax, __reduce_max_sync(0xffffffffu, tb));
         }
-        H2 = H1; w2 = w1;
-        H1 = h; E1 = ev; F1 = fv; w1 = clo;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) { H2[c] = H1[c]; H1[c] = h[c]; E1[c] = ev[c]; F1[c] = fv[c]; }
+        w2 = w1; W2 = W1; w1 = clo; W1 = W;
         l2lo = l1lo; l2hi = l1hi;
-        if (live) { l1lo = clo + __ffs(live) - 1; l1hi = clo + 31 - __clz(live); }
-        else { l1lo = 1; l1hi = 0; }
+        if (live[0] | live[1]) {
+            l1lo = clo + (live[0] ? __ffs(live[0]) - 1 : 32 + __ffs(live[1]) - 1);
+            l1hi = clo + (live[1] ? 63 - __clz(live[1]) : 31 - __clz(live[0]));
+        } else {
+            l1lo = 1; l1hi = 0;
+        }
     }
     *amax_out = amax;
     *bmax_out = bmax;
     return true;
+}
+
+// Pass 2 over every pair pass 1 scored: one warp per pair, a few pairs per grab.
+__global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, const int64_t *qoffsets,
+                                                         const uint8_t *tcodes, const int64_t *toffsets,
+                                                         const pastis_cand *pairs, int64_t n_pairs,
+                                                         const int8_t *gmat, int o, int e, const int16_t *bm_all,
+                                                         const int64_t *bm_off, unsigned long long *next_pair,
+                                                         sw_score_out *res) {
+    __shared__ int s_mat[PASTIS_NSYM * PASTIS_NSYM];
+    for (int x = threadIdx.x; x < PASTIS_NSYM * PASTIS_NSYM; x += blockDim.x) s_mat[x] = gmat[x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    constexpr int GRAB = 4;
+    for (;;) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(next_pair, (unsigned long long)GRAB);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= (unsigned long long)n_pairs) break;
+        for (int u = 0; u < GRAB; ++u) {
+            const int64_t p = (int64_t)g + u;
+            if (p >= n_pairs) break;
+            const sw_score_out r = res[p];
+            if (r.big || r.score <= 0) continue;
+            const pastis_cand c = pairs[p];
+            int amax = 0, bmax = 0;
+            if (band_walk(qcodes + qoffsets[c.i], tcodes + toffsets[c.j], s_mat, o, e, r.score, r.end_i, r.end_j,
+                          bm_all + bm_off[p], &amax, &bmax) &&
+                amax > 0 && bmax > 0 && lane == 0) {
+                res[p].rect_i = r.end_i + 1 - amax;
+                res[p].rect_j = r.end_j + 1 - bmax;
+            }                                      // else: the whole up-left rectangle (0, 0)
+        }
+    }
+}
+
+// Row-pair bound entries of each pair: (query length + 1) / 2.
+__global__ void k_bm_count(const pastis_cand *pairs, int64_t n, const int64_t *qoffsets, int64_t *cnt) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int i = pairs[p].i;
+    cnt[p] = (qoffsets[i + 1] - qoffsets[i] + 1) / 2;
 }
 
 __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcodes, const int64_t *qoffsets,
@@ -299,17 +371,15 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                                                          const pastis_cand *pairs, const int64_t *seg_start,
                                                          int64_t n_seg, const int8_t *gmat, int o, int e,
                                                          int max_s, int prow_cap, char *scratch, size_t warp_bytes,
-                                                         int sstride, int *next_seg, sw_score_out *out,
+                                                         int sstride, int *next_seg, int16_t *bm_all,
+                                                         const int64_t *bm_off, sw_score_out *out,
                                                          unsigned long long *cells) {
-    // dynamic shared memory: profile [NRES][prow_cap] int16, then per warp two row-pair
-    // bound arrays [prow_cap / 2] int16
+    // dynamic shared memory: the profile [NRES][prow_cap] int16
     extern __shared__ __align__(16) int16_t s_prof[];
     __shared__ int s_seg, s_next;
     __shared__ uint32_t s_key[SEG_MAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * SW_WARPS + warp;
-    int16_t *bmA = s_prof + NRES * prow_cap + warp * prow_cap;
-    int16_t *bmB = bmA + prow_cap / 2;
     uint2 *my = reinterpret_cast<uint2 *>(scratch + (size_t)gw * warp_bytes);
     const bool packable = o + e <= GAP_MAX;
     unsigned long long my_cells = 0;
@@ -333,12 +403,13 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                                                                  : 0);
             }
         }
-        // the segment's pairs by target length, so that the two pairs of a warp match
+        // the segment's pairs by target length, longest first, so that the two pairs of
+        // a warp match and the last pairs taken are the shortest
         if (threadIdx.x < SEG_MAX) {
             uint32_t key = 0xFFFFFFFFu;
             if ((int)threadIdx.x < cnt) {
                 const int j = pairs[p0 + threadIdx.x].j;
-                key = ((uint32_t)(toffsets[j + 1] - toffsets[j]) << 6) | threadIdx.x;
+                key = ((uint32_t)(65535 - (toffsets[j + 1] - toffsets[j])) << 7) | threadIdx.x;
             }
             s_key[threadIdx.x] = key;
         }
@@ -362,7 +433,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
             int nn[2], st[2];                                     // st: 0 zero, 1 big, 2 run
             const uint8_t *tp[2];
             for (int u = 0; u < 2; ++u) {
-                pp[u] = pk + u < cnt ? p0 + (int64_t)(s_key[pk + u] & 63u) : -1;
+                pp[u] = pk + u < cnt ? p0 + (int64_t)(s_key[pk + u] & (SEG_MAX - 1)) : -1;
                 nn[u] = 0; st[u] = 0; tp[u] = tcodes;
                 if (pp[u] < 0) continue;
                 const pastis_cand c = pairs[pp[u]];
@@ -378,16 +449,17 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
             if (st[0] == 2 || st[1] == 2) {
                 // both halves busy; a lone pair fills both
                 const int ua = st[0] == 2 ? 0 : 1, ub = st[1] == 2 ? 1 : 0;
+                int16_t *bma = bm_all + bm_off[pp[ua]], *bmb = bm_all + bm_off[pp[ub]];
                 end_cell ea, eb;
 #define PASTIS_SW_CASE(L)                                                                                       \
     case L:                                                                                                     \
-        score_pair<L>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bmA, bmB, &ea, &eb); \
+        score_pair<L>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bma, bmb, &ea, &eb); \
         break;
                 switch (lr) {
                     PASTIS_SW_CASE(2) PASTIS_SW_CASE(4) PASTIS_SW_CASE(6) PASTIS_SW_CASE(8)
                     PASTIS_SW_CASE(10) PASTIS_SW_CASE(12) PASTIS_SW_CASE(14)
                     default:
-                        score_pair<16>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bmA, bmB,
+                        score_pair<16>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bma, bmb,
                                        &ea, &eb);
                         break;
                 }
@@ -401,16 +473,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                 sw_score_out r;
                 r.score = 0; r.end_i = 0; r.end_j = 0; r.rect_i = 0; r.rect_j = 0; r.big = st[u] == 1;
                 if (st[u] == 2) {
-                    if (res[u].h > 0) {
-                        r.score = res[u].h; r.end_i = res[u].i; r.end_j = res[u].j;
-                        const int16_t *bm = (u == 0 || st[0] != 2) ? bmA : bmB;
-                        int amax = 0, bmax = 0;
-                        if (bound_band(s_prof, prow, tp[u], o, e, r.score, r.end_i, r.end_j, bm, &amax, &bmax) &&
-                            amax > 0 && bmax > 0) {
-                            r.rect_i = r.end_i + 1 - amax;
-                            r.rect_j = r.end_j + 1 - bmax;
-                        }                                         // else: the whole up-left rectangle
-                    }
+                    if (res[u].h > 0) { r.score = res[u].h; r.end_i = res[u].i; r.end_j = res[u].j; }
                     my_cells += (unsigned long long)m * (unsigned long long)nn[u];
                 }
                 if (lane == 0) out[pp[u]] = r;
@@ -730,6 +793,14 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
 
 }  // namespace
 
+cudaError_t sw_set_smem_limit(size_t bytes) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_sw_score);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sw_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(bytes - fa.sharedSizeBytes));
+}
+
 // Host side of the Smith-Waterman path (called by pastis_align_pairs after validation).
 pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, const uint8_t *d_tcodes,
                        const int64_t *d_toffsets, const pastis_cand *d_pairs,
@@ -753,15 +824,28 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_nseg, soff + n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
 
+    // row-pair bounds of pass 1 for pass 2: (query length + 1) / 2 int16 per pair
+    int64_t *bm_cnt;
+    PASTIS_WS(bm_cnt, ctx, WS_ALN_BOFF, sizeof(int64_t) * (2 * (size_t)n_pairs + 1));
+    int64_t *bm_off = bm_cnt + n_pairs;
+    k_bm_count<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, bm_cnt);
+    PASTIS_LAUNCHED(ctx);
+    s = exclusive_scan_i64(ctx, bm_cnt, bm_off, n_pairs);
+    if (s != PASTIS_OK) return s;
+    int64_t h_bm = 0;
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_bm, bm_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    int16_t *bm_all;
+    PASTIS_WS(bm_all, ctx, WS_ALN_BOUND, sizeof(int16_t) * (size_t)h_bm + 16);
+
     sw_score_out *res;
     PASTIS_WS(res, ctx, WS_ALN_PASS1, sizeof(sw_score_out) * (size_t)n_pairs);
     // pass 1+2: profile rows up to the longest query (in whole stripes), within shared memory
     int prow_cap = ((lmax + STRIPE1 - 1) / STRIPE1) * STRIPE1;
     if (prow_cap < STRIPE1) prow_cap = STRIPE1;
-    auto shm_for = [](int pc) { return (size_t)NRES * pc * 2 + (size_t)SW_WARPS * pc * 2; };
+    auto shm_for = [](int pc) { return (size_t)NRES * pc * 2; };
     while (prow_cap > STRIPE1 && shm_for(prow_cap) + 1024 > ctx->smem_optin) prow_cap -= STRIPE1;
     const size_t shm1 = shm_for(prow_cap);
-    cudaFuncSetAttribute(k_sw_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm1);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sw_score, SW_THREADS, shm1);
     if (per_sm < 1) per_sm = 1;
@@ -777,7 +861,17 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     k_sw_score<<<blocks1, SW_THREADS, shm1, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, seg_start,
                                                   (int64_t)h_nseg, dmat,
                                                   p->gap_open, p->gap_extend, max_s, prow_cap, (char *)scratch,
-                                                  warp_bytes, sstride, flags + 1, res, (unsigned long long *)d_cells);
+                                                  warp_bytes, sstride, flags + 1, bm_all, bm_off, res,
+                                                  (unsigned long long *)d_cells);
+    PASTIS_LAUNCHED(ctx);
+    prof_end(ctx);
+    int per_sm2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_sw_bound, SW_THREADS, 0);
+    if (per_sm2 < 1) per_sm2 = 1;
+    prof_begin(ctx, "sw_pass2");
+    k_sw_bound<<<ctx->sm_count * per_sm2, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                               n_pairs, dmat, p->gap_open, p->gap_extend, bm_all,
+                                                               bm_off, (unsigned long long *)(flags + 10), res);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     prof_begin(ctx, "sw_pass3");
