@@ -324,6 +324,112 @@ __device__ bool band_walk(const uint8_t *__restrict__ q, const uint8_t *__restri
     return true;
 }
 
+// The value the previous row holds at window index idx (two columns per lane; NEG
+// outside the window).  `wide` (the previous row used its second chunk) is the same
+// on every lane.
+__device__ __forceinline__ int row_get(const int (&X)[2], int idx, bool wide) {
+    const int v0 = __shfl_sync(0xffffffffu, X[0], idx & 31);
+    int v = v0;
+    if (wide) {
+        const int v1 = __shfl_sync(0xffffffffu, X[1], idx & 31);
+        v = idx >= 32 ? v1 : v0;
+    }
+    return (unsigned)idx < (wide ? 64u : 32u) ? v : NEG;
+}
+
+// The same reverse DP row by row, for o >= e: lane L holds columns c0 + L and
+// c0 + 32 + L of reverse row a, where c0 is the first live column of row a - 1 (no
+// cell left of it has a live predecessor).  E along the row is an exclusive prefix
+// maximum over the columns to the left, taken over max(D, F): with o >= e a gap that
+// E itself opened never beats extending E, and as the threshold is the same along a
+// row, a gap run through a cell below it stays below it.  So the live cells and their
+// values are those of the antidiagonal form.  Returns false when a row needs more
+// than 64 columns.
+__device__ bool band_rows(const uint8_t *__restrict__ q, const uint8_t *__restrict__ t, const int *s_mat, int o,
+                          int e, int S, int ei, int ej, const int16_t *__restrict__ bm, int *amax_out,
+                          int *bmax_out) {
+    const int lane = threadIdx.x & 31;
+    const int A = ei + 1, B = ej + 1;
+    const int slack = max(o - e, 0);
+    int Hp[2] = {NEG, NEG}, Fp[2] = {NEG, NEG};        // row a - 1 at columns c0p + 32 c + lane
+    int c0p = 0, plo = 0, phi = -1;                     // its window start and live columns
+    bool pwide = false;
+    int amax = 0, bmax = 0;
+    for (int a = 0; a <= A; ++a) {
+        if (a > 0 && phi < plo) break;                  // row a - 1 had no live cell
+        const int c0 = a == 0 ? 0 : plo;
+        if (a > 0 && phi + 1 > c0 + 63) return false;   // its diagonal successors leave the window
+        const int i = ei - a + 1;                       // forward row of this reverse row
+        const int thr = S - (i >= 1 ? (int)bm[(i - 1) >> 1] : 0) - slack;
+        const int qa = a >= 1 ? (int)q[i] * PASTIS_NSYM : 0;
+        const int dsh = c0 - c0p;
+        int H[2] = {NEG, NEG}, F[2] = {NEG, NEG};
+        unsigned live[2] = {0u, 0u};
+        int carry = NEG;                                // max of max(D, F) + k e left of the chunk
+        int tb = -1;                                    // this lane's largest column reaching S
+        bool wide = false;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c == 1) {
+                // the second chunk when row a - 1 reaches past the first, or an E run
+                // leaves it still at or above the threshold
+                const int e_next = carry - o - 31 * e;
+                if (!(phi + 1 > c0 + 31 || e_next >= thr)) break;
+                wide = true;
+            }
+            const int k = 32 * c + lane, b = c0 + k;
+            const int src = k + dsh;
+            const int hb = row_get(Hp, src, pwide), fb = row_get(Fp, src, pwide);
+            const int hd = row_get(Hp, src - 1, pwide);
+            int hh = NEG, fv = NEG;
+            if (b <= B) {
+                if (a >= 1) {
+                    fv = max(max(hb - o, fb - e), NEG);
+                    const int dv = (b >= 1 && hd != NEG) ? hd + s_mat[qa + (int)t[ej - b + 1]] : NEG;
+                    hh = max(dv, fv);
+                } else if (b == 0) {
+                    hh = 0;                             // the end cell
+                }
+            }
+            int incl = hh > NEG ? hh + k * e : NEG;
+#pragma unroll
+            for (int x = 1; x < 32; x <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, x);
+                if (lane >= x) incl = max(incl, y);
+            }
+            int excl = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane == 0) excl = NEG;
+            excl = max(excl, carry);
+            carry = max(carry, __shfl_sync(0xffffffffu, incl, 31));
+            const int ev = (b >= 1 && excl > NEG) ? excl - o - (k - 1) * e : NEG;
+            int h = max(hh, ev);
+            if (b > B || h < thr) { h = NEG; fv = NEG; }
+            H[c] = h; F[c] = fv;
+            live[c] = __ballot_sync(0xffffffffu, h != NEG);
+            if (h == S) tb = b;
+        }
+        if (wide) {
+            // a live run still going past the second chunk needs more than 64 columns
+            if (carry - o - 63 * e >= thr) return false;
+        }
+        if (__any_sync(0xffffffffu, tb >= 0)) {
+            amax = a;
+            bmax = max(bmax, __reduce_max_sync(0xffffffffu, tb < 0 ? 0 : tb));
+        }
+        Hp[0] = H[0]; Hp[1] = H[1]; Fp[0] = F[0]; Fp[1] = F[1];
+        c0p = c0; pwide = wide;
+        if (live[0] | live[1]) {
+            plo = c0 + (live[0] ? __ffs(live[0]) - 1 : 32 + __ffs(live[1]) - 1);
+            phi = c0 + (live[1] ? 63 - __clz(live[1]) : 31 - __clz(live[0]));
+        } else {
+            plo = 1; phi = 0;
+        }
+    }
+    *amax_out = amax;
+    *bmax_out = bmax;
+    return true;
+}
+
 // Pass 2 over every pair pass 1 scored: one warp per pair, a few pairs per grab.
 __global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, const int64_t *qoffsets,
                                                          const uint8_t *tcodes, const int64_t *toffsets,
@@ -348,9 +454,11 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, 
             if (r.big || r.score <= 0) continue;
             const pastis_cand c = pairs[p];
             int amax = 0, bmax = 0;
-            if (band_walk(qcodes + qoffsets[c.i], tcodes + toffsets[c.j], s_mat, o, e, r.score, r.end_i, r.end_j,
-                          bm_all + bm_off[p], &amax, &bmax) &&
-                amax > 0 && bmax > 0 && lane == 0) {
+            const uint8_t *qp = qcodes + qoffsets[c.i], *tp = tcodes + toffsets[c.j];
+            const int16_t *bm = bm_all + bm_off[p];
+            bool ok = o >= e && band_rows(qp, tp, s_mat, o, e, r.score, r.end_i, r.end_j, bm, &amax, &bmax);
+            if (!ok) ok = band_walk(qp, tp, s_mat, o, e, r.score, r.end_i, r.end_j, bm, &amax, &bmax);
+            if (ok && amax > 0 && bmax > 0 && lane == 0) {
                 res[p].rect_i = r.end_i + 1 - amax;
                 res[p].rect_j = r.end_j + 1 - bmax;
             }                                      // else: the whole up-left rectangle (0, 0)
