@@ -34,8 +34,9 @@ import synth  # noqa: E402
 
 METRIC = "edges/s (whole path: k-mers, A.S.A^T candidates, SW alignment, ANI/coverage filter)"
 UNIT = "edges/s"
-OPS_PER_CELL = 11          # int32 lane-ops per SW cell: E 3, F 3, H 4, running best 1
-INT_LANES_PER_SM = 128     # int32 lanes per SM per clock
+OPS_PER_CELL = 11          # integer ops per SW cell: E 3, F 3, H 4, running best 1
+INT_LANES_PER_SM = 128     # 32-bit integer lanes per SM per clock
+HALVES_PER_LANE = 2        # SW pass 1 works on 16-bit halves, two per 32-bit lane op
 N_SM = 152
 
 WORKLOADS = {
@@ -501,10 +502,11 @@ def main():
         per_launch_cells = total_cells / max(1, n_l)
         achieved = per_launch_cells * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
         sm_max = (clk or {}).get("sm_max_mhz", 2070.0) or 2070.0
-        peak = N_SM * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+        peak = N_SM * INT_LANES_PER_SM * HALVES_PER_LANE * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "sw_pass1",
-                "peak_note": f"{N_SM} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz (derived, not measured)",
+                "peak_note": (f"{N_SM} SMs x {INT_LANES_PER_SM} 32-bit lanes x {HALVES_PER_LANE} 16-bit halves x "
+                              f"{sm_max:.0f} MHz (derived, not measured)"),
                 "ops_per_cell": OPS_PER_CELL}
 
     cpu = None
@@ -524,7 +526,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (SW pass 1) / int32", "data": "synthetic",
             "config": {"workload": w["desc"], "name": name, "sequences": ps.n, "residues": int(ps.ascii.size),
                        "batch": (f"one of {batches} equal-work query-row blocks (rows i against every j > i); "
                                  f"the blocks together are the whole all-vs-all job"),
