@@ -14,7 +14,7 @@
 //   one 32-bit add advances both.  Lane l owns up to 16 consecutive query rows and at
 //   step s computes column j = s - l, taking H/F of the row above from lane l-1
 //   (__shfl_up_sync).  Scores come from a biased query profile in shared memory
-//   (int16, [target residue][query row]) shared by every warp of the CTA.  Each row
+//   (one byte per [target residue][query row]) shared by every warp of the CTA.  Each row
 //   keeps a key (H << 16 | 65535 - j) of its first maximum; the end is the first row
 //   with the best score, at that row's first maximum: the row-major first maximum.
 //   Pass 1 also stores, per pair of query rows, the largest H it met there.
@@ -88,6 +88,19 @@ constexpr int PAD_RES = PASTIS_NSYM;       // stands for target columns past the
 
 __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) { return __vmaxs2(a, b); }
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) { return __byte_perm(a, b, sel); }
+// prmt with the sign-replicate bit of its selector (bytes below 0x80 become 0x00)
+__device__ __forceinline__ uint32_t prmt_sx(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// a * b + c as a multiply-add (b is the run-time 1 the kernel receives, so the add goes
+// to the multiply-add pipe and leaves the integer ALU pipe to the maxima)
+__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
 
 struct end_cell { int h, i, j; };
 
@@ -99,47 +112,35 @@ __device__ __forceinline__ int rows_per_lane(int m) {
     return min(16, max(2, (per + 1) & ~1));
 }
 
-// One column of a lane's LR rows for both pairs.  prof rows are biased scores
-// (score + BIAS, 0 for the pad residue and for rows past the query).  The key of a row
-// keeps (Ho << 16 | 65535 - j) of its best column: the largest Ho, then the first
-// column, i.e. the first maximum of that row.
+// The profile holds one byte per (target residue, query row): score + BIAS, 0 for the
+// pad residue and past the query.  Rows are laid out per stripe and lane in 16-byte
+// slots (slot of lane l in stripe st at st * 512 + l * 16, row r of the lane at +r), so
+// a lane reads its rows of one column with a single 16-byte load.
+constexpr int SLOT = 16;
+constexpr int STRIPE_BYTES = 32 * SLOT;
+
+// One column of a lane's LR rows for both pairs.  The key of a row keeps
+// (Ho << 16 | 65535 - j) of its best column: the largest Ho, then the first column,
+// i.e. the first maximum of that row.
 template <int LR>
-__device__ __forceinline__ void column2(const int16_t *__restrict__ pa, const int16_t *__restrict__ pb,
+__device__ __forceinline__ void column2(const uint8_t *__restrict__ pa, const uint8_t *__restrict__ pb,
                                         uint32_t (&Ho)[LR], uint32_t (&E)[LR], uint32_t (&kA)[LR],
                                         uint32_t (&kB)[LR], uint32_t hdiag, uint32_t &f, uint32_t &hup, uint32_t jt,
-                                        uint32_t OP, uint32_t EP, uint32_t KD) {
+                                        uint32_t one, uint32_t nOP, uint32_t nEP, uint32_t KD) {
     constexpr uint32_t Z = (uint32_t)BIAS * P2;
-    uint32_t wa[LR / 2], wb[LR / 2];
-    if (LR % 8 == 0) {
-        const uint4 *va = reinterpret_cast<const uint4 *>(pa), *vb = reinterpret_cast<const uint4 *>(pb);
-#pragma unroll
-        for (int k = 0; k < LR / 8; ++k) {
-            const uint4 x = va[k], y = vb[k];
-            wa[4 * k] = x.x; wa[4 * k + 1] = x.y; wa[4 * k + 2] = x.z; wa[4 * k + 3] = x.w;
-            wb[4 * k] = y.x; wb[4 * k + 1] = y.y; wb[4 * k + 2] = y.z; wb[4 * k + 3] = y.w;
-        }
-    } else if (LR % 4 == 0) {
-        const uint2 *va = reinterpret_cast<const uint2 *>(pa), *vb = reinterpret_cast<const uint2 *>(pb);
-#pragma unroll
-        for (int k = 0; k < LR / 4; ++k) {
-            const uint2 x = va[k], y = vb[k];
-            wa[2 * k] = x.x; wa[2 * k + 1] = x.y;
-            wb[2 * k] = y.x; wb[2 * k + 1] = y.y;
-        }
-    } else {
-        const uint32_t *va = reinterpret_cast<const uint32_t *>(pa), *vb = reinterpret_cast<const uint32_t *>(pb);
-#pragma unroll
-        for (int k = 0; k < LR / 2; ++k) { wa[k] = va[k]; wb[k] = vb[k]; }
-    }
+    const uint4 x = *reinterpret_cast<const uint4 *>(pa), y = *reinterpret_cast<const uint4 *>(pb);
+    const uint32_t wa[4] = {x.x, x.y, x.z, x.w}, wb[4] = {y.x, y.y, y.z, y.w};
+    // byte r of the two words into the low and high halves, zero-extended
+    constexpr uint32_t SEL[4] = {0xc480u, 0xd591u, 0xe6a2u, 0xf7b3u};
 #pragma unroll
     for (int r = 0; r < LR; ++r) {
-        const uint32_t s = prmt(wa[r >> 1], wb[r >> 1], (r & 1) ? 0x7632u : 0x5410u);
+        const uint32_t s = prmt_sx(wa[r >> 2], wb[r >> 2], SEL[r & 3]);
         const uint32_t d = hdiag + s + KD;                 // H(i-1, j-1) + score
-        E[r] = vmax2(Ho[r], E[r] - EP);                    // E(i, j) from H(i, j-1) - o and E(i, j-1)
-        f = vmax2(hup, f - EP);                            // F(i, j) from H(i-1, j) - o and F(i-1, j)
+        E[r] = vmax2(Ho[r], madd(E[r], one, nEP));         // E(i, j) from H(i, j-1) - o and E(i, j-1) - e
+        f = vmax2(hup, madd(f, one, nEP));                 // F(i, j) from H(i-1, j) - o and F(i-1, j) - e
         const uint32_t h = vmax2(vmax2(d, E[r]), vmax2(f, Z));
         hdiag = Ho[r];
-        Ho[r] = h - OP;
+        Ho[r] = madd(h, one, nOP);
         hup = Ho[r];
         kA[r] = (uint32_t)max((int)kA[r], (int)prmt(Ho[r], jt, 0x1054u));
         kB[r] = (uint32_t)max((int)kB[r], (int)prmt(Ho[r], jt, 0x3254u));
@@ -152,17 +153,18 @@ __device__ __forceinline__ void column2(const int16_t *__restrict__ pa, const in
 // lane l-1; a stripe is 32 * LR rows, its last row handed on through buf.  Columns
 // past the shorter target use the pad residue, which scores -64 against every row: a
 // cell there stays below the best score of its own pair, so it never becomes the end.
-// Returns each pair's best score and its first maximum in row-major order, and
-// writes bm[g] = the largest H on rows 2g and 2g+1 (an upper bound used by pass 2).
+// Lane 0 takes the target residues from a window of 32 columns that the warp loads one
+// window ahead.  Returns each pair's best score and its first maximum in row-major
+// order, and writes bm[g] = the largest H on rows 2g and 2g+1 (pass 2's bound).
 template <int LR>
-__device__ void score_pair(const int16_t *__restrict__ prof, int prow, const uint8_t *__restrict__ tA, int nA,
-                           const uint8_t *__restrict__ tB, int nB, int m, int o, int e, uint2 *buf, int sstride,
-                           int16_t *bmA, int16_t *bmB, end_cell *ra, end_cell *rb) {
+__device__ void score_pair(const uint8_t *__restrict__ prof, int prow8, const uint8_t *__restrict__ tA, int nA,
+                           const uint8_t *__restrict__ tB, int nB, int m, int o, int e, uint32_t one, uint2 *buf,
+                           int sstride, int16_t *bmA, int16_t *bmB, end_cell *ra, end_cell *rb) {
     constexpr int STRIPE = 32 * LR;
     const int lane = threadIdx.x & 31;
     const int n = max(nA, nB);
     const uint32_t INIT = (uint32_t)(BIAS - o) * P2;       // x = -o in both halves
-    const uint32_t OP = (uint32_t)o * P2, EP = (uint32_t)e * P2;
+    const uint32_t nOP = 0u - (uint32_t)o * P2, nEP = 0u - (uint32_t)e * P2;
     const uint32_t KD = (uint32_t)(o - BIAS) * P2;         // d = Ho(i-1, j-1) + o + score: bias folded in
     int bA = -1, iA = 0, jA = 0, bB = -1, iB = 0, jB = 0;
     const int nstripes = (m + STRIPE - 1) / STRIPE;
@@ -176,23 +178,32 @@ __device__ void score_pair(const int16_t *__restrict__ prof, int prow, const uin
         const uint2 *in_buf = buf + (size_t)(stripe & 1) * sstride;
         uint2 *out_buf = buf + (size_t)((stripe + 1) & 1) * sstride;
         const bool last = stripe + 1 == nstripes;
-        const int16_t *pr = prof + row0;
+        const uint8_t *pr = prof + stripe * STRIPE_BYTES + lane * SLOT;
+        // target residues of columns [w, w + 32) (lane k holds column w + k), and the next window
+        uint32_t twin = (lane < nA ? (uint32_t)tA[lane] : (uint32_t)PAD_RES) |
+                        ((lane < nB ? (uint32_t)tB[lane] : (uint32_t)PAD_RES) << 16);
+        uint32_t tnext = (32 + lane < nA ? (uint32_t)tA[32 + lane] : (uint32_t)PAD_RES) |
+                         ((32 + lane < nB ? (uint32_t)tB[32 + lane] : (uint32_t)PAD_RES) << 16);
         for (int s = 0; s < n + 31; ++s) {
             const int j = s - lane;
+            if (s > 0 && (s & 31) == 0) {
+                twin = tnext;
+                const int c = s + 32 + lane;
+                tnext = (c < nA ? (uint32_t)tA[c] : (uint32_t)PAD_RES) | ((c < nB ? (uint32_t)tB[c] : (uint32_t)PAD_RES) << 16);
+            }
+            const uint32_t tw = __shfl_sync(0xffffffffu, twin, s & 31);
             uint32_t hu = __shfl_up_sync(0xffffffffu, out_h, 1);
             uint32_t fu = __shfl_up_sync(0xffffffffu, out_f, 1);
             uint32_t tt = __shfl_up_sync(0xffffffffu, out_t, 1);
-            if (lane == 0 && j < n) {
-                const uint32_t ca = j < nA ? (uint32_t)tA[j] : (uint32_t)PAD_RES;
-                const uint32_t cb = j < nB ? (uint32_t)tB[j] : (uint32_t)PAD_RES;
-                tt = ca | (cb << 16);
+            if (lane == 0) {
+                tt = tw;
                 if (stripe == 0) { hu = INIT; fu = INIT; }
-                else { const uint2 c = in_buf[j]; hu = c.x; fu = c.y; }
+                else if (j < n) { const uint2 c = in_buf[j]; hu = c.x; fu = c.y; }
             }
             if (j >= 0 && j < n) {
                 uint32_t f = fu, hup = hu;
-                column2<LR>(pr + (int)(tt & 0xFFFFu) * prow, pr + (int)(tt >> 16) * prow, Ho, E, kA, kB, hd, f, hup,
-                            65535u - (uint32_t)j, OP, EP, KD);
+                column2<LR>(pr + (int)(tt & 0xFFFFu) * prow8, pr + (int)(tt >> 16) * prow8, Ho, E, kA, kB, hd, f,
+                            hup, 65535u - (uint32_t)j, one, nOP, nEP, KD);
                 hd = hu;
                 out_h = hup; out_f = f; out_t = tt;
                 if (lane == 31 && !last) out_buf[j] = make_uint2(hup, f);
@@ -478,12 +489,12 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                                                          const uint8_t *tcodes, const int64_t *toffsets,
                                                          const pastis_cand *pairs, const int64_t *seg_start,
                                                          int64_t n_seg, const int8_t *gmat, int o, int e,
-                                                         int max_s, int prow_cap, char *scratch, size_t warp_bytes,
-                                                         int sstride, int *next_seg, int16_t *bm_all,
-                                                         const int64_t *bm_off, sw_score_out *out,
+                                                         int max_s, int prow_cap, uint32_t one, char *scratch,
+                                                         size_t warp_bytes, int sstride, int *next_seg,
+                                                         int16_t *bm_all, const int64_t *bm_off, sw_score_out *out,
                                                          unsigned long long *cells) {
-    // dynamic shared memory: the profile [NRES][prow_cap] int16
-    extern __shared__ __align__(16) int16_t s_prof[];
+    // dynamic shared memory: the profile [NRES][prow_cap] bytes (prow_cap a whole number of stripes)
+    extern __shared__ __align__(16) uint8_t s_prof[];
     __shared__ int s_seg, s_next;
     __shared__ uint32_t s_key[SEG_MAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -502,13 +513,17 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
         const int64_t qo = qoffsets[qi];
         const int m = (int)(qoffsets[qi + 1] - qo);
         const int lr = rows_per_lane(m);
-        const int prow = ((m + 32 * lr - 1) / (32 * lr)) * (32 * lr);
-        // query profile: prof[c][i] = M[q_i][c] + BIAS; 0 for the pad residue and past the query
-        if (prow <= prow_cap) {
-            for (int x = threadIdx.x; x < NRES * prow; x += blockDim.x) {
-                const int c = x / prow, i = x - c * prow;
-                s_prof[x] = (int16_t)((i < m && c < PASTIS_NSYM) ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] + BIAS
-                                                                 : 0);
+        const int prow8 = ((m + 32 * lr - 1) / (32 * lr)) * STRIPE_BYTES;     // profile bytes per residue
+        // query profile: byte (st * 512 + l * 16 + r) of residue c = M[q_i][c] + BIAS for row
+        // i = st * 32 * lr + l * lr + r of the query; 0 for the pad residue, unused slots
+        // and rows past the query
+        if (prow8 <= prow_cap) {
+            for (int x = threadIdx.x; x < NRES * prow8; x += blockDim.x) {
+                const int c = x / prow8, rest = x - c * prow8;
+                const int st = rest / STRIPE_BYTES, l = (rest % STRIPE_BYTES) / SLOT, r = rest % SLOT;
+                const int i = st * 32 * lr + l * lr + r;
+                s_prof[x] = (uint8_t)((r < lr && i < m && c < PASTIS_NSYM)
+                                          ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] + BIAS : 0);
             }
         }
         // the segment's pairs by target length, longest first, so that the two pairs of
@@ -549,7 +564,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                 nn[u] = (int)(toffsets[c.j + 1] - to);
                 tp[u] = tcodes + to;
                 if (m == 0 || nn[u] == 0) st[u] = 0;
-                else if (!packable || prow > prow_cap || (int64_t)max_s * (int64_t)min(m, nn[u]) >= SCORE_MAX) st[u] = 1;
+                else if (!packable || prow8 > prow_cap || (int64_t)max_s * (int64_t)min(m, nn[u]) >= SCORE_MAX) st[u] = 1;
                 else st[u] = 2;
             }
             end_cell res[2];
@@ -561,14 +576,14 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                 end_cell ea, eb;
 #define PASTIS_SW_CASE(L)                                                                                       \
     case L:                                                                                                     \
-        score_pair<L>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bma, bmb, &ea, &eb); \
+        score_pair<L>(s_prof, prow8, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, one, my, sstride, bma, bmb, &ea, &eb); \
         break;
                 switch (lr) {
                     PASTIS_SW_CASE(2) PASTIS_SW_CASE(4) PASTIS_SW_CASE(6) PASTIS_SW_CASE(8)
                     PASTIS_SW_CASE(10) PASTIS_SW_CASE(12) PASTIS_SW_CASE(14)
                     default:
-                        score_pair<16>(s_prof, prow, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, my, sstride, bma, bmb,
-                                       &ea, &eb);
+                        score_pair<16>(s_prof, prow8, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, one, my, sstride, bma,
+                                       bmb, &ea, &eb);
                         break;
                 }
 #undef PASTIS_SW_CASE
@@ -951,7 +966,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     // pass 1+2: profile rows up to the longest query (in whole stripes), within shared memory
     int prow_cap = ((lmax + STRIPE1 - 1) / STRIPE1) * STRIPE1;
     if (prow_cap < STRIPE1) prow_cap = STRIPE1;
-    auto shm_for = [](int pc) { return (size_t)NRES * pc * 2; };
+    auto shm_for = [](int pc) { return (size_t)NRES * pc; };
     while (prow_cap > STRIPE1 && shm_for(prow_cap) + 1024 > ctx->smem_optin) prow_cap -= STRIPE1;
     const size_t shm1 = shm_for(prow_cap);
     int per_sm = 0;
@@ -968,7 +983,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     prof_begin(ctx, "sw_pass1");
     k_sw_score<<<blocks1, SW_THREADS, shm1, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, seg_start,
                                                   (int64_t)h_nseg, dmat,
-                                                  p->gap_open, p->gap_extend, max_s, prow_cap, (char *)scratch,
+                                                  p->gap_open, p->gap_extend, max_s, prow_cap, 1u, (char *)scratch,
                                                   warp_bytes, sstride, flags + 1, bm_all, bm_off, res,
                                                   (unsigned long long *)d_cells);
     PASTIS_LAUNCHED(ctx);
