@@ -25,7 +25,7 @@ EDGE_DTYPE = np.dtype([("i", "<i4"), ("j", "<i4"), ("ident", "<u2"), ("cols", "<
                        ("score", "<i4"), ("weight", "<f4")])
 assert CAND_DTYPE.itemsize == 20 and ALN_DTYPE.itemsize == 20 and EDGE_DTYPE.itemsize == 20
 
-SW, XD = 0, 1
+SW, XD, SW_SCORE = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -63,6 +63,10 @@ def lib():
                                          P, ctypes.POINTER(i64)]
             L.or_filter.restype = i64
             L.or_filter.argtypes = [P, P, P, i64, i32, i32, P]
+            L.or_ns_edges.restype = i64
+            L.or_ns_edges.argtypes = [P, P, P, i64, P]
+            L.or_components.restype = ctypes.c_int
+            L.or_components.argtypes = [i32, P, i64, P]
             L.or_free.restype = None
             L.or_free.argtypes = [P]
             _lib = L
@@ -153,6 +157,46 @@ def filter_edges(offsets, pairs, alns, ani=30, cov=70) -> np.ndarray:
     out = np.zeros(max(1, p.size), EDGE_DTYPE)
     ne = lib().or_filter(_ptr(o), _ptr(p), _ptr(a), p.size, ani, cov, _ptr(out))
     return out[:ne].copy()
+
+
+def ns_edges(offsets, pairs, alns) -> np.ndarray:
+    """Edges weighted by the normalized score (Sec. VI-B, NS): every pair with a positive
+    score, weight = score / shorter length in float32."""
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    p = np.ascontiguousarray(pairs, dtype=CAND_DTYPE)
+    a = np.ascontiguousarray(alns, dtype=ALN_DTYPE)
+    out = np.zeros(max(1, p.size), EDGE_DTYPE)
+    ne = lib().or_ns_edges(_ptr(o), _ptr(p), _ptr(a), p.size, _ptr(out))
+    return out[:ne].copy()
+
+
+def components(n, edges) -> np.ndarray:
+    """Connected components (Sec. VI-B): label = smallest vertex of the component."""
+    e = np.ascontiguousarray(edges, dtype=EDGE_DTYPE)
+    lab = np.zeros(max(1, n), np.int32)
+    if lib().or_components(int(n), _ptr(e), e.size, _ptr(lab)) != 0:
+        raise ValueError("edge endpoint out of range")
+    return lab[:n].copy()
+
+
+def weighted_precision_recall(labels, families):
+    """Weighted precision and recall of a clustering against reference families (the
+    measures of protein clustering studies the paper uses, Sec. VI-B): precision = sum
+    over clusters of the largest family overlap / N; recall = sum over families of the
+    largest cluster overlap / N."""
+    labels = np.asarray(labels, dtype=np.int64)
+    families = np.asarray(families, dtype=np.int64)
+    n = labels.size
+    if n == 0:
+        return 1.0, 1.0
+    pairs = np.stack([labels, families], axis=1)
+    uniq, counts = np.unique(pairs, axis=0, return_counts=True)
+    best_c = {}
+    best_f = {}
+    for (c, f), k in zip(uniq.tolist(), counts.tolist()):
+        best_c[c] = max(best_c.get(c, 0), k)
+        best_f[f] = max(best_f.get(f, 0), k)
+    return sum(best_c.values()) / n, sum(best_f.values()) / n
 
 
 def run(ascii, offsets, matrix, k=6, m=0, min_shared=1, mode=SW, xdrop=49, gap_open=11,

@@ -16,6 +16,8 @@
  *   or_xd              x-drop seed-and-extend                     Sec. IV-E, Sec. VI
  *   or_align_pairs     SW or XD over a candidate list             Sec. IV-E
  *   or_filter          ANI / coverage similarity filter -> edges  Sec. IV-F, VI-B
+ *   or_ns_edges        edges weighted by the normalized score     Sec. VI-B (NS)
+ *   or_components      connected components of the edge graph    Sec. VI-B (components)
  *
  * Readings where the paper is silent are stated beside the code that takes them.
  * Parity unpinned: the pruning order inside or_xd and the symmetrization rule inside
@@ -632,10 +634,16 @@ int or_align_pairs(const uint8_t *codes, const int64_t *offsets, const or_cand *
         int32_t lt = (int32_t)(offsets[c->j + 1] - offsets[c->j]);
         span_stats best;
         int used = 0, ok = 0;
-        if (mode == 0) {
+        if (mode == 0 || mode == 2) {
             or_sw(q, lq, t, lt, mat, o, e, &best);
             if (cells) *cells += (int64_t)lq * lt;
             ok = passes(&best, lq, lt, ani, cov);
+            if (mode == 2) {
+                /* score and end only (what the NS weight needs, Sec. VI-B: no traceback) */
+                best.qb = best.tb = 0;
+                best.ident = best.cols = 0;
+                ok = 0;
+            }
         } else {
             int ns = (c->count >= 2 && c->qpos[1] != 0xFFFF) ? 2 : 1;
             for (int s = 0; s < ns; ++s) {
@@ -656,6 +664,51 @@ int or_align_pairs(const uint8_t *codes, const int64_t *offsets, const or_cand *
         r->ident = (uint16_t)best.ident; r->cols = (uint16_t)best.cols;
         r->seed_used = (uint8_t)used; r->passes = (uint8_t)ok; r->pad = 0;
     }
+    return 0;
+}
+
+/* NS edges (Sec. VI-B): the raw score normalized by the shorter sequence, which needs
+ * no traceback.  Reading: weight = score / min(|s_i|, |s_j|) in float32; the ANI and
+ * coverage tests need the traceback and do not apply, so every pair with a positive
+ * score is an edge.  Input (i, j) order. */
+int64_t or_ns_edges(const int64_t *offsets, const or_cand *pairs, const or_aln *alns, int64_t n_pairs,
+                    or_edge *out) {
+    int64_t ne = 0;
+    for (int64_t p = 0; p < n_pairs; ++p) {
+        if (alns[p].score <= 0) continue;
+        int64_t lq = offsets[pairs[p].i + 1] - offsets[pairs[p].i];
+        int64_t lt = offsets[pairs[p].j + 1] - offsets[pairs[p].j];
+        int64_t ls = lq < lt ? lq : lt;
+        or_edge *x = &out[ne++];
+        x->i = pairs[p].i; x->j = pairs[p].j;
+        x->ident = alns[p].ident; x->cols = alns[p].cols; x->score = alns[p].score;
+        x->weight = (float)alns[p].score / (float)ls;
+    }
+    return ne;
+}
+
+/* Connected components of the graph on n vertices with the given edges (the paper's
+ * components-as-families variant, Sec. VI-B).  label[v] = the smallest vertex of v's
+ * component: union-find that always hangs the larger root under the smaller one. */
+static int32_t uf_find(int32_t *parent, int32_t v) {
+    while (parent[v] != v) {
+        parent[v] = parent[parent[v]];
+        v = parent[v];
+    }
+    return v;
+}
+
+int or_components(int32_t n, const or_edge *edges, int64_t n_edges, int32_t *label) {
+    for (int32_t v = 0; v < n; ++v) label[v] = v;
+    for (int64_t x = 0; x < n_edges; ++x) {
+        int32_t a = edges[x].i, b = edges[x].j;
+        if (a < 0 || b < 0 || a >= n || b >= n) return 1;
+        a = uf_find(label, a);
+        b = uf_find(label, b);
+        if (a < b) label[b] = a;
+        else if (b < a) label[a] = b;
+    }
+    for (int32_t v = 0; v < n; ++v) label[v] = uf_find(label, v);
     return 0;
 }
 
