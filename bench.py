@@ -307,6 +307,88 @@ def run_prefilter(args):
 
 
 # ---------------------------------------------------------------------------------
+# variants of the graph (Sec. VI-B): components as families, CK threshold, NS weight
+# ---------------------------------------------------------------------------------
+def weighted_pr(labels, families):
+    """Weighted precision (each cluster's largest family share) and recall (each
+    family's largest cluster share) of a clustering, both over all proteins."""
+    labels = np.asarray(labels, np.int64)
+    families = np.asarray(families, np.int64)
+    key = labels * (int(families.max()) + 1) + families
+    k, cnt = np.unique(key, return_counts=True)
+    lab_of, fam_of = k // (int(families.max()) + 1), k % (int(families.max()) + 1)
+    best_l = np.zeros(int(labels.max()) + 1, np.int64)
+    best_f = np.zeros(int(families.max()) + 1, np.int64)
+    np.maximum.at(best_l, lab_of, cnt)
+    np.maximum.at(best_f, fam_of, cnt)
+    return float(best_l.sum()) / labels.size, float(best_f.sum()) / labels.size
+
+
+def run_variants(args):
+    """On the 20,000-protein set of the bench recipe (whole all-vs-all job per run):
+    connected components of the ANI graph as protein families for m in {0, 10, 25, 50},
+    scored by weighted precision / recall against the planted families (the paper's
+    components table); the common-k-mer threshold t = 3 (min_shared 4) with 25
+    substitutes; and the NS weight (score only, no traceback) against ANI at m = 25."""
+    import torch
+    from paper_2009_14467_gb300 import pastis as P
+    dev = torch.device("cuda", 0)
+    name = "zipf_20k_s25_sw"
+    ps = make_set(name)
+    a = torch.from_numpy(ps.ascii).to(dev)
+    o = torch.from_numpy(ps.offsets).to(dev)
+    ctx = P.Context(0)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1000.0
+
+    def ani_run(m, min_shared=1):
+        params = P.Params(matrix=synth.blosum62(), k=6, m_subs=m, min_shared=min_shared)
+        r = P.run(ctx, a, o, params)
+        lab = P.components(ctx, ps.n, r["edges"])
+        return r, lab
+
+    rows = []
+    ani_run(25)                                             # warm-up
+    for m, ms in ((0, 1), (10, 1), (25, 1), (50, 1), (25, 4)):
+        (r, lab), t = timed(lambda: ani_run(m, ms))
+        prec, rec = weighted_pr(lab.cpu().numpy(), ps.family)
+        rows.append({"m": m, "min_shared": ms, "candidates": int(r["cands"].shape[0]),
+                     "edges": int(r["edges"].shape[0]), "components": int(np.unique(lab.cpu().numpy()).size),
+                     "precision": round(prec, 4), "recall": round(rec, 4), "s": round(t, 3),
+                     "edges_per_s": r["edges"].shape[0] / t})
+
+    def ns_run():
+        params = P.Params(matrix=synth.blosum62(), k=6, m_subs=25, mode=P.SW_SCORE)
+        codes = P.encode(ctx, a)
+        A = P.build_kmers(ctx, codes, o, 6)
+        cands = P.overlap_spgemm(ctx, A, params)
+        alns = P.align_pairs(ctx, codes, o, cands, params)
+        return P.ns_edges(ctx, o, cands, alns)
+
+    ns_run()
+    e_ns, t_ns = timed(ns_run)
+    ani25 = rows[2]
+    line = {"metric": ("graph variants (Sec. VI-B) on 20,000 proteins: whole-job time with the ANI weight over "
+                       "the NS weight at m = 25 (NS needs no traceback)"),
+            "value": ani25["s"] / t_ns, "unit": "x", "higher_is_better": True,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "dtype": "int16x2 / int32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[name]["desc"] + "; whole all-vs-all job per run", "name": name},
+            "components_as_families": rows,
+            "ns": {"edges": int(e_ns.shape[0]), "s": round(t_ns, 3), "edges_per_s": e_ns.shape[0] / t_ns,
+                   "weight": "score / shorter length, every pair with a positive score, no traceback"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------------
 # serving: query batches against a resident database
 # ---------------------------------------------------------------------------------
 def run_serve(args):
@@ -383,9 +465,9 @@ def main():
                     help="equal-work query-row blocks the job is split into (default: 8 for 100k sets, else 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
-    ap.add_argument("--mode", default="plain", choices=["plain", "prefilter", "serve"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "prefilter", "serve", "variants"],
                     help="plain: the exact path (the headline); prefilter: learned prefilter vs plain; "
-                         "serve: query batches against a resident database")
+                         "serve: query batches against a resident database; variants: components, CK, NS")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests in the stream")
     ap.add_argument("--slots", type=int, default=4, help="serve mode: concurrent worker slots")
     ap.add_argument("--recall", type=float, default=0.995, help="edge recall the prefilter must keep")
@@ -401,6 +483,8 @@ def main():
         return run_prefilter(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "variants":
+        return run_variants(args)
 
     import torch
     import torch.distributed as dist

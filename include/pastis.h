@@ -56,8 +56,8 @@ enum {
     PASTIS_ERR_INTERNAL = 8          /* a device-side consistency check failed             */
 };
 
-/* Alignment modes (Sec. IV-E). */
-enum { PASTIS_SW = 0, PASTIS_XD = 1 };
+/* Alignment modes (Sec. IV-E; PASTIS_SW_SCORE for the NS weight of Sec. VI-B). */
+enum { PASTIS_SW = 0, PASTIS_XD = 1, PASTIS_SW_SCORE = 2 };
 
 /* Parameters of the method (Sec. VI: k = 6, BLOSUM62, gap open 11, extension 1,
  * x-drop 49, common-k-mer threshold; Sec. IV-F: ANI 30%, coverage 70%).          */
@@ -66,7 +66,7 @@ typedef struct pastis_params {
     int32_t m_subs;       /* substitute k-mers per k-mer, 0 = exact matching, <= 128     */
     int32_t min_shared;   /* candidate iff it shares >= min_shared k-mers; the paper's  */
                           /* "common k-mer threshold t" drops <= t, i.e. min_shared=t+1 */
-    int32_t mode;         /* PASTIS_SW or PASTIS_XD                                      */
+    int32_t mode;         /* PASTIS_SW, PASTIS_XD or PASTIS_SW_SCORE                     */
     int32_t xdrop;        /* X of the x-drop extension (49)                              */
     int32_t gap_open;     /* a gap of length L costs gap_open + (L-1)*gap_extend         */
     int32_t gap_extend;
@@ -226,6 +226,8 @@ pastis_status pastis_query_overlap(pastis_ctx *ctx, const pastis_kmat *Q, const 
  *   and to the left (antidiagonal order; a cell dies when H < best - xdrop); among
  *   the seeds whose alignment passes the filter the higher score (first seed on
  *   ties) is kept, otherwise the best score with passes = 0.
+ * PASTIS_SW_SCORE: the Smith-Waterman score and end only (what the NS weight needs;
+ *   no traceback): score, qe, te as in PASTIS_SW; qb, tb, ident, cols, passes are 0.
  * d_offsets has n_seqs+1 entries; a pair naming a sequence outside [0, n_seqs), or
  * (XD) a seed that does not fit its sequence, gives PASTIS_ERR_INVALID_ARG before any
  * alignment runs.  d_cells (optional, device int64) accumulates the DP cells computed
@@ -294,6 +296,26 @@ pastis_status pastis_filter_edges_qt(pastis_ctx *ctx, const int64_t *d_qoffsets,
                                      const int64_t *d_toffsets, int32_t n_t, const pastis_cand *d_pairs,
                                      const pastis_aln *d_alns, int64_t n_pairs, const pastis_params *params,
                                      pastis_edge *d_out, int64_t capacity, int64_t *n_out);
+
+/* ---- variants of the graph (Sec. VI-B) ------------------------------------------ */
+
+/* NS edges: every pair with a positive score becomes an edge (i, j, ident, cols, score,
+ * weight = score / min(|s_i|, |s_j|) as a correctly rounded float32), in pair order.
+ * The NS weight needs no traceback, so alignments from PASTIS_SW_SCORE suffice; the
+ * ANI and coverage tests need one and are not applied.  Capacity protocol and errors
+ * as pastis_filter_edges.  Synchronises.                                              */
+pastis_status pastis_ns_edges(pastis_ctx *ctx, const int64_t *d_offsets, int32_t n_seqs,
+                              const pastis_cand *d_pairs, const pastis_aln *d_alns, int64_t n_pairs,
+                              pastis_edge *d_out, int64_t capacity, int64_t *n_out);
+
+/* Connected components of the graph on n_seqs vertices whose edges are d_edges[n_edges]
+ * (only i and j are read), for the components-as-families variant (Sec. VI-B).
+ * d_labels[n_seqs] receives, for each vertex, the smallest vertex of its component, so
+ * the result does not depend on the order of the edges.  An endpoint outside
+ * [0, n_seqs) gives PASTIS_ERR_INVALID_ARG; PASTIS_ERR_INTERNAL if a bounded union-find
+ * walk runs out (it cannot on a valid input).  Synchronises.                           */
+pastis_status pastis_components(pastis_ctx *ctx, int32_t n_seqs, const pastis_edge *d_edges, int64_t n_edges,
+                                int32_t *d_labels);
 
 /* ---- a10 without allocation ---------------------------------------------------------
  * The paper has no counterpart of this call: it is pastis_filter_edges (same keep rule

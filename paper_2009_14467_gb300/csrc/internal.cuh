@@ -20,7 +20,7 @@ enum ws_slot {
     WS_SPG_ROWWORK, WS_SPG_ROWOFF, WS_SPG_ROWCNT, WS_SPG_TMP, WS_SPG_TABLE, WS_SPG_BIN,
     WS_SPG_RESULT,
     WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER, WS_ALN_BOUND, WS_ALN_BOFF,
-    WS_FILT_FLAGS, WS_FILT_SCAN,
+    WS_FILT_FLAGS, WS_FILT_SCAN, WS_CC,
     WS_MLP,
     WS_COUNT
 };

@@ -829,8 +829,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                                                          const pastis_cand *pairs, int64_t n_pairs,
                                                          const int8_t *gmat, int o, int e, int ani, int cov,
                                                          stripe3_cell *scratch, int sstride, int *next_pair,
-                                                         const sw_score_out *res, pastis_aln *out, int *err,
-                                                         unsigned long long *cells) {
+                                                         const sw_score_out *res, int score_only, pastis_aln *out,
+                                                         int *err, unsigned long long *cells) {
     __shared__ int s_mat[(PASTIS_NSYM + 1) * 32];
     for (int x = threadIdx.x; x < (PASTIS_NSYM + 1) * 32; x += blockDim.x) {
         const int a = x / 32, b = x % 32;
@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
         g1.score = 0; g1.big = 0; g1.end_i = g1.end_j = g1.rect_i = g1.rect_j = 0;
         if (pg < n_pairs) {
             g1 = res[pg];
-            if (!g1.big && g1.score > 0 && g1.end_i + 1 - g1.rect_i <= GROWS) {
+            if (!score_only && !g1.big && g1.score > 0 && g1.end_i + 1 - g1.rect_i <= GROWS) {
                 const pastis_cand c = pairs[pg];
                 gm = g1.end_i + 1 - g1.rect_i;
                 gn = g1.end_j + 1 - g1.rect_j;
@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
             const int64_t p = p0 + k;
             if (p >= n_pairs) break;
             const sw_score_out r1 = res[p];
-            const bool small = !r1.big && r1.score > 0 && r1.end_i + 1 - r1.rect_i <= GROWS;
+            const bool small = !score_only && !r1.big && r1.score > 0 && r1.end_i + 1 - r1.rect_i <= GROWS;
             if (small) continue;
             const pastis_cand c = pairs[p];
             const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
@@ -896,8 +896,13 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                     if (h > 0)
                         finish_record(rec, h, bi, bj, (int)(beg >> 16), (int)(beg & 0xFFFF), (int)(im >> 16),
                                       (int)(im & 0xFFFF), lq, lt, ani, cov);
+                    if (score_only) { rec.qb = rec.tb = 0; rec.ident = rec.cols = 0; rec.passes = 0; }
                     if (lane == 0) my_cells += (unsigned long long)lq * lt;
                 }
+            } else if (r1.score > 0 && score_only) {
+                rec.score = r1.score;                       // score and end only
+                rec.qe = (uint16_t)(r1.end_i + 1);
+                rec.te = (uint16_t)(r1.end_j + 1);
             } else if (r1.score > 0) {
                 const int ri = r1.rect_i, rj = r1.rect_j;
                 int h, dummy_i, dummy_j;
@@ -988,20 +993,24 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
                                                   (unsigned long long *)d_cells);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
+    const int score_only = p->mode == PASTIS_SW_SCORE;
     int per_sm2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_sw_bound, SW_THREADS, 0);
     if (per_sm2 < 1) per_sm2 = 1;
-    prof_begin(ctx, "sw_pass2");
-    k_sw_bound<<<ctx->sm_count * per_sm2, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
-                                                               n_pairs, dmat, p->gap_open, p->gap_extend, bm_all,
-                                                               bm_off, (unsigned long long *)(flags + 10), res);
-    PASTIS_LAUNCHED(ctx);
-    prof_end(ctx);
+    if (!score_only) {                         // the score mode needs no begin, so no rectangle
+        prof_begin(ctx, "sw_pass2");
+        k_sw_bound<<<ctx->sm_count * per_sm2, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets,
+                                                                   d_pairs, n_pairs, dmat, p->gap_open, p->gap_extend,
+                                                                   bm_all, bm_off, (unsigned long long *)(flags + 10),
+                                                                   res);
+        PASTIS_LAUNCHED(ctx);
+        prof_end(ctx);
+    }
     prof_begin(ctx, "sw_pass3");
     k_sw_carry<<<blocks3, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, dmat,
                                                p->gap_open,
                                                p->gap_extend, p->ani_min_pct, p->cov_min_pct,
-                                               (stripe3_cell *)scratch, sstride, flags + 8, res, d_out, flags,
+                                               (stripe3_cell *)scratch, sstride, flags + 8, res, score_only, d_out, flags,
                                                (unsigned long long *)d_cells);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);

@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
-SW, XD = 0, 1
+SW, XD, SW_SCORE = 0, 1, 2
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_RESIDUE", 3: "CAPACITY", 4: "OUT_OF_MEMORY",
           5: "CUDA", 6: "TIMEOUT", 7: "UNSUPPORTED", 8: "INTERNAL"}
@@ -297,6 +297,37 @@ def filter_edges(ctx: Context, offsets: torch.Tensor, pairs: torch.Tensor, alns:
                                                             _ptr(alns), n, ctypes.byref(p), _ptr(out), cap,
                                                             ctypes.byref(nout)))
     return out[:nout.value]
+
+
+def _variant_sigs(L):
+    if not getattr(L, "_variant_sigs", False):
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.pastis_ns_edges.argtypes = [P, P, i32, P, P, i64, P, i64, ctypes.POINTER(i64)]
+        L.pastis_ns_edges.restype = i32
+        L.pastis_components.argtypes = [P, i32, P, i64, P]
+        L.pastis_components.restype = i32
+        L._variant_sigs = True
+    return L
+
+
+def ns_edges(ctx: Context, offsets: torch.Tensor, pairs: torch.Tensor, alns: torch.Tensor) -> torch.Tensor:
+    """pastis_ns_edges: edges weighted by score / shorter length (uint8 [n, 20]), pair order."""
+    L = _variant_sigs(lib())
+    n = pairs.shape[0]
+    nout = ctypes.c_int64()
+    cap = max(1, n)
+    out = torch.empty((cap, REC_BYTES), dtype=torch.uint8, device=offsets.device)
+    _check("pastis_ns_edges", L.pastis_ns_edges(ctx.h, _ptr(offsets), offsets.numel() - 1, _ptr(pairs), _ptr(alns),
+                                                n, _ptr(out), cap, ctypes.byref(nout)))
+    return out[:nout.value]
+
+
+def components(ctx: Context, n_seqs: int, edges: torch.Tensor) -> torch.Tensor:
+    """pastis_components: int32 label per sequence = smallest sequence of its component."""
+    L = _variant_sigs(lib())
+    labels = torch.empty(max(1, n_seqs), dtype=torch.int32, device=edges.device)
+    _check("pastis_components", L.pastis_components(ctx.h, n_seqs, _ptr(edges), edges.shape[0], _ptr(labels)))
+    return labels[:n_seqs]
 
 
 FILTER_STATIC_MAX_PAIRS = 4194304      # PASTIS_FILTER_STATIC_MAX_PAIRS
