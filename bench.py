@@ -47,6 +47,10 @@ WORKLOADS = {
         "SW int32 BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
     "zipf_20k_s25_sw": dict(n=20_000, m=25, mode=0, desc="20,000 proteins, same recipe (smaller stand-in)"),
     "zipf_5k_s25_sw": dict(n=5_000, m=25, mode=0, desc="5,000 proteins, same recipe (profiling stand-in)"),
+    "zipf_1m_xd": dict(n=1_000_000, m=0, mode=1, desc=(
+        "1,000,000 proteins: 100,000 Zipf(1.5, 1-200) families (80%) + 20% singletons, lengths log-normal"
+        "(median 300) clipped 50-2000, same mutation recipe; k=6 exact k-mers, min_shared 1, x-drop (X = 49) "
+        "from both seeds, BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
     "families_1k_sw": dict(n=1000, m=0, mode=0, desc=(
         "1,000 proteins = 100 families x 10, k=6 exact, SW int32, ANI 30 / cov 70")),
 }
@@ -87,6 +91,8 @@ def make_set(name, seed_offset=0):
     w = WORKLOADS[name]
     if name.startswith("families_1k"):
         return synth.families_1k(seed=1 + seed_offset)
+    if name == "zipf_1m_xd":
+        return synth.zipf_1m(seed=3 + seed_offset)
     return synth.zipf_100k(seed=2 + seed_offset, n=w["n"])
 
 
@@ -182,7 +188,7 @@ def run_reference(args):
         cells += c
     value = edges / secs if secs > 0 else 0.0
     sample = (f"{args.steps} steps, each the oracle's whole path on {block} random sequences of the "
-              f"set ({block * (block - 1) // 2} uniformly random pairs); {pairs} pairs, {cells} SW cells, "
+              f"set ({block * (block - 1) // 2} uniformly random pairs); {pairs} pairs, {cells} DP cells, "
               f"{edges} edges in {secs:.2f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / max(1, args.steps),
@@ -513,7 +519,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    batches = args.batches or (8 if ps.n >= 50_000 else 1)
+    batches = args.batches or (64 if ps.n >= 500_000 else 8 if ps.n >= 50_000 else 1)
     blocks = row_blocks(ps.n, batches)
     counter = [0]
 
@@ -593,6 +599,36 @@ def main():
                               f"{sm_max:.0f} MHz (derived, not measured)"),
                 "ops_per_cell": OPS_PER_CELL}
 
+    if "xd_extend" in prof and "sw_pass1" not in prof:
+        # x-drop: int32 recurrence with carries, computed live cells
+        n_l, ms_l = prof["xd_extend"]
+        sm_max = (clk or {}).get("sm_max_mhz", 2070.0) or 2070.0
+        achieved = total_cells / max(1, n_l) * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
+        peak = N_SM * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "xd_extend",
+                "peak_note": f"{N_SM} SMs x {INT_LANES_PER_SM} 32-bit lanes x {sm_max:.0f} MHz (derived, not measured)",
+                "ops_per_cell": OPS_PER_CELL, "cells": "computed cells of the x-drop extensions"}
+    sw_block = None
+    if w["mode"] == 1 and rank == 0:
+        # full SW over one block's candidates (the sample of the x-drop workload's pairs)
+        sw_params = P.Params(matrix=mat, k=6, m_subs=w["m"], mode=0)
+        codes = P.encode(ctx, ascii_dev)
+        A = P.build_kmers(ctx, codes, offs_dev, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=blocks[0])
+        del A
+        c_sw = torch.zeros(1, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.align_pairs(ctx, codes, offs_dev, cands, sw_params, c_sw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        sw_block = {"pairs": int(cands.shape[0]), "s": t, "pairs_per_s": cands.shape[0] / t,
+                    "gcups": int(c_sw.item()) / t / 1e9,
+                    "sample": "all candidates of row block 0 of the job (a fixed, seeded block of query rows)"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(777)
@@ -603,14 +639,16 @@ def main():
             e += de; s += dt; p += dp; c += dc
         cpu = {"value": e / s if s > 0 else 0.0, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": (f"oracle whole path on random blocks of {args.ref_block} sequences of the same set: "
-                          f"{p} uniformly random pairs, {c} SW cells, {e} edges in {s:.1f} s on 1 host core")}
+                          f"{p} uniformly random pairs, {c} DP cells, {e} edges in {s:.1f} s on 1 host core")}
 
     if rank == 0:
         kernel_ms = {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if w["mode"] == 0 else METRIC.replace("SW alignment", "x-drop alignment"),
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (SW pass 1) / int32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "dtype": "int16x2 (SW pass 1) / int32" if w["mode"] == 0 else "int32",
             "config": {"workload": w["desc"], "name": name, "sequences": ps.n, "residues": int(ps.ascii.size),
                        "batch": (f"one of {batches} equal-work query-row blocks (rows i against every j > i); "
                                  f"the blocks together are the whole all-vs-all job"),
@@ -622,6 +660,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": roof, "dominant_kernel": dominant, "kernel_ms_timed_region": kernel_ms,
+            "sw_on_block": sw_block,
             "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

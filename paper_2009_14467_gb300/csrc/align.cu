@@ -131,6 +131,111 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
     res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
 }
 
+// The same extension with the band in registers: lane L holds band cells L and 32 + L
+// of an antidiagonal (band index = a - start of that antidiagonal's computed range),
+// neighbours on the two antidiagonals before come by shuffles, the live range by a
+// ballot and the best cell by two reductions: the largest H, then the smallest a
+// holding it, as above.  Returns false (nothing written) when an antidiagonal
+// needs more than 64 cells; the caller then runs xd_extend_warp.
+constexpr int XD_BAND = 64;
+
+template <typename T>
+__device__ __forceinline__ T xd_get(const T (&X)[2], int idx, bool wide, T none) {
+    const T v0 = __shfl_sync(0xffffffffu, X[0], idx & 31);
+    T v = v0;
+    if (wide) {
+        const T v1 = __shfl_sync(0xffffffffu, X[1], idx & 31);
+        v = idx >= 32 ? v1 : v0;
+    }
+    return (unsigned)idx < (wide ? 64u : 32u) ? v : none;
+}
+
+__device__ bool xd_band_warp(const uint8_t *q, int A, int qs, const uint8_t *t, int B, int ts, const int *s_mat,
+                             int o, int e, int X, ext_out *res) {
+    const int lane = threadIdx.x & 31;
+    // antidiagonal d-1 (start w1, computed width W1) and d-2 (w2, W2); d = 0 is the anchor
+    int H1[2] = {lane == 0 ? 0 : NEG, NEG}, E1[2] = {NEG, NEG}, F1[2] = {NEG, NEG};
+    uint32_t HC1[2] = {0u, 0u}, EC1[2] = {0u, 0u}, FC1[2] = {0u, 0u};
+    int H2[2] = {NEG, NEG};
+    uint32_t HC2[2] = {0u, 0u};
+    int w1 = 0, W1 = 1, w2 = 0, W2 = 0;
+    int best = 0, ba = 0, bb = 0;
+    uint32_t bc = 0;
+    long long cells = 1;
+    int llo = 0, lhi = 0;
+    for (int d = 1; d <= A + B; ++d) {
+        const int clo = max(max(llo, d - B), 0);
+        const int chi = min(min(lhi + 1, A), d);
+        if (clo > chi) break;
+        const int W = chi - clo + 1;
+        if (W > XD_BAND) return false;
+        const bool wide = W > 32 || W1 > 32 || W2 > 32;
+        int h[2] = {NEG, NEG}, ev[2] = {NEG, NEG}, fv[2] = {NEG, NEG};
+        uint32_t hc[2] = {0u, 0u}, evc[2] = {0u, 0u}, fvc[2] = {0u, 0u};
+        unsigned live[2] = {0u, 0u};
+        int myh = NEG, mya = 0x7FFFFFFF;             // this lane's best live cell (largest H, smallest a)
+        uint32_t myc = 0u;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c == 1 && !wide) break;
+            const int a = clo + 32 * c + lane, b = d - a;
+            const int i1 = a - w1, i2 = a - 1 - w2;
+            const int h1a = xd_get(H1, i1, wide, NEG), e1a = xd_get(E1, i1, wide, NEG);
+            const uint32_t hc1a = xd_get(HC1, i1, wide, 0u), ec1a = xd_get(EC1, i1, wide, 0u);
+            const int h1u = xd_get(H1, i1 - 1, wide, NEG), f1u = xd_get(F1, i1 - 1, wide, NEG);
+            const uint32_t hc1u = xd_get(HC1, i1 - 1, wide, 0u), fc1u = xd_get(FC1, i1 - 1, wide, 0u);
+            const int h2 = xd_get(H2, i2, wide, NEG);
+            const uint32_t hc2 = xd_get(HC2, i2, wide, 0u);
+            if (a <= chi) {
+                if (b >= 1 && i1 >= 0 && i1 < W1) {
+                    const int eo = h1a - o, ex = e1a - e;
+                    if (eo >= ex) { ev[c] = eo; evc[c] = hc1a; } else { ev[c] = ex; evc[c] = ec1a; }
+                    if (ev[c] < NEG) ev[c] = NEG;
+                }
+                if (a >= 1 && i1 - 1 >= 0 && i1 - 1 < W1) {
+                    const int fo = h1u - o, fx = f1u - e;
+                    if (fo >= fx) { fv[c] = fo; fvc[c] = hc1u; } else { fv[c] = fx; fvc[c] = fc1u; }
+                    if (fv[c] < NEG) fv[c] = NEG;
+                }
+                int dv = NEG;
+                uint32_t dvc = 0u;
+                if (a >= 1 && b >= 1 && i2 >= 0 && i2 < W2 && h2 != NEG) {
+                    const int qa = q[(long long)(a - 1) * qs], tb = t[(long long)(b - 1) * ts];
+                    dv = h2 + s_mat[qa * 32 + tb];
+                    dvc = hc2 + (qa == tb ? 0x10001u : 1u);
+                }
+                int hh = dv;
+                uint32_t hcc = dvc;
+                if (fv[c] > hh) { hh = fv[c]; hcc = fvc[c]; }
+                if (ev[c] > hh) { hh = ev[c]; hcc = evc[c]; }
+                if (hh < best - X) { hh = NEG; ev[c] = NEG; fv[c] = NEG; }
+                h[c] = hh; hc[c] = hcc;
+                if (hh != NEG && hh > myh) { myh = hh; mya = a; myc = hcc; }   // chunk 0 first: smaller a
+            }
+            live[c] = __ballot_sync(0xffffffffu, h[c] != NEG);
+        }
+        cells += W;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            H2[c] = H1[c]; HC2[c] = HC1[c];
+            H1[c] = h[c]; E1[c] = ev[c]; F1[c] = fv[c]; HC1[c] = hc[c]; EC1[c] = evc[c]; FC1[c] = fvc[c];
+        }
+        w2 = w1; W2 = W1; w1 = clo; W1 = W;
+        if (!(live[0] | live[1])) break;
+        const int toph = __reduce_max_sync(0xffffffffu, myh);
+        if (toph > best) {
+            const int ta = (int)__reduce_min_sync(0xffffffffu, myh == toph ? (unsigned)mya : 0xFFFFFFFFu);
+            const unsigned who = __ballot_sync(0xffffffffu, myh == toph && mya == ta);
+            bc = __shfl_sync(0xffffffffu, myc, __ffs(who) - 1);
+            best = toph; ba = ta; bb = d - ta;
+        }
+        llo = clo + (live[0] ? __ffs(live[0]) - 1 : 32 + __ffs(live[1]) - 1);
+        lhi = clo + (live[1] ? 63 - __clz(live[1]) : 31 - __clz(live[0]));
+    }
+    res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
+    return true;
+}
+
 __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, const int64_t *qoffsets,
                                                         const uint8_t *tcodes, const int64_t *toffsets,
                                                         const pastis_cand *pairs, int64_t n_pairs, int k,
@@ -161,12 +266,11 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, c
             const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
             const int lq = (int)(qoffsets[c.i + 1] - qo), lt = (int)(toffsets[c.j + 1] - to);
             const int pi = c.qpos[seed], pj = c.tpos[seed];
-            if (!left)
-                xd_extend_warp(qcodes + qo + pi + k, lq - pi - k, 1, tcodes + to + pj + k, lt - pj - k, 1, s_mat, o,
-                               e, X, buf, W, &r);
-            else
-                xd_extend_warp(qcodes + qo + pi - 1, pi, -1, tcodes + to + pj - 1, pj, -1, s_mat, o, e, X, buf, W,
-                               &r);
+            const uint8_t *qa = left ? qcodes + qo + pi - 1 : qcodes + qo + pi + k;
+            const uint8_t *ta = left ? tcodes + to + pj - 1 : tcodes + to + pj + k;
+            const int A = left ? pi : lq - pi - k, B = left ? pj : lt - pj - k, st = left ? -1 : 1;
+            if (!xd_band_warp(qa, A, st, ta, B, st, s_mat, o, e, X, &r))
+                xd_extend_warp(qa, A, st, ta, B, st, s_mat, o, e, X, buf, W, &r);
         }
         if (lane == 0) out[task] = r;
         __syncwarp();
@@ -297,7 +401,12 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     if (hf[5]) return PASTIS_ERR_INVALID_RESIDUE;
     const int lmax = hf[2];
     if (lmax > PASTIS_MAX_LEN) return PASTIS_ERR_INVALID_ARG;
-    const int blocks = ctx->sm_count * 2;
+    int xd_per_sm = 2;
+    if (xd) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xd_per_sm, k_xd_ext, ALN_THREADS, 0);
+        if (xd_per_sm < 1) xd_per_sm = 1;
+    }
+    const int blocks = ctx->sm_count * xd_per_sm;
     const int nwarps = blocks * ALN_WARPS;
     if (!xd) {
         s = sw_align(ctx, d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params, dmat, flags, lmax,
