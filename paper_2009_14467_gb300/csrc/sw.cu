@@ -73,21 +73,17 @@ __global__ void k_seg_starts(const uint32_t *flags, const uint32_t *off, int64_t
 // ---------------------------------------------------------------------------------
 // pass 1: two pairs per warp, one in each 16-bit half of every register
 // ---------------------------------------------------------------------------------
-// Values are stored biased, v = x + BIAS per half.  Every state of the recurrence
-// stays in [0, 32767] when o + e <= GAP_MAX, the scores lie in [-64, 63] and no score
-// can reach SCORE_MAX: H >= 0, E and F >= -o (a gap is at least as good as opening it
-// from H >= 0), and the largest value is the best score plus one substitution.  So
-// plain 32-bit adds and subtracts never carry between the halves, and the signed
-// 16x2 maximum compares both pairs at once.
-constexpr int BIAS = 64;
-constexpr int GAP_MAX = 60;
+// Every state is a signed 16-bit half: H >= 0, E and F >= -o (a gap is at least as good
+// as opening it from H >= 0), and nothing exceeds the best score plus one substitution,
+// so with no score reaching SCORE_MAX all values fit.  Per-half adds wrap within their
+// half, and the 16x2 maximum instructions (max(a + b, c) and max(a, b, c, 0)) advance
+// both pairs at once.  The profile stores score + o in a signed byte, so o <= GAP_MAX.
+constexpr int GAP_MAX = 64;
 constexpr int SCORE_MAX = 32000;
 constexpr uint32_t P2 = 0x00010001u;
 constexpr int NRES = PASTIS_NSYM + 1;      // profile rows: the residues, then the pad residue
 constexpr int PAD_RES = PASTIS_NSYM;       // stands for target columns past the shorter target
 
-__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) { return __vmaxs2(a, b); }
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) { return __byte_perm(a, b, sel); }
 // prmt with the sign-replicate bit of its selector (bytes below 0x80 become 0x00)
 __device__ __forceinline__ uint32_t prmt_sx(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t d;
@@ -112,38 +108,39 @@ __device__ __forceinline__ int rows_per_lane(int m) {
     return min(16, max(2, (per + 1) & ~1));
 }
 
-// The profile holds one byte per (target residue, query row): score + BIAS, 0 for the
-// pad residue and past the query.  Rows are laid out per stripe and lane in 16-byte
-// slots (slot of lane l in stripe st at st * 512 + l * 16, row r of the lane at +r), so
-// a lane reads its rows of one column with a single 16-byte load.
+// The profile holds one signed byte per (target residue, query row): score + o, and
+// o - 64 (the lowest score) for the pad residue and past the query.  Rows are laid out
+// per stripe and lane in 16-byte slots (slot of lane l in stripe st at st * 512 + l * 16,
+// row r of the lane at +r), so a lane reads its rows of one column with one 16-byte load.
 constexpr int SLOT = 16;
 constexpr int STRIPE_BYTES = 32 * SLOT;
 
-// One column of a lane's LR rows for both pairs.  The key of a row keeps
-// (Ho << 16 | 65535 - j) of its best column: the largest Ho, then the first column,
-// i.e. the first maximum of that row.
+// One column of a lane's LR rows for both pairs.  Ho = H - o is kept per row (it feeds
+// E, F and the keys), so the diagonal term is Ho(i-1, j-1) + (score + o).  The key of a
+// row keeps (Ho << 16 | 65535 - j) of its best column as a signed word: the largest Ho,
+// then the first column, i.e. the first maximum of that row.  Pair A's key is
+// Ho * 2^16 + jt (pair B's half leaves the word), pair B's is (Ho & 0xFFFF0000) | jt.
 template <int LR>
 __device__ __forceinline__ void column2(const uint8_t *__restrict__ pa, const uint8_t *__restrict__ pb,
                                         uint32_t (&Ho)[LR], uint32_t (&E)[LR], uint32_t (&kA)[LR],
                                         uint32_t (&kB)[LR], uint32_t hdiag, uint32_t &f, uint32_t &hup, uint32_t jt,
-                                        uint32_t one, uint32_t nOP, uint32_t nEP, uint32_t KD) {
-    constexpr uint32_t Z = (uint32_t)BIAS * P2;
+                                        uint32_t sh16, uint32_t OP, uint32_t nEP) {
     const uint4 x = *reinterpret_cast<const uint4 *>(pa), y = *reinterpret_cast<const uint4 *>(pb);
     const uint32_t wa[4] = {x.x, x.y, x.z, x.w}, wb[4] = {y.x, y.y, y.z, y.w};
-    // byte r of the two words into the low and high halves, zero-extended
+    // byte r of the two words into the low and high halves, sign-extended
     constexpr uint32_t SEL[4] = {0xc480u, 0xd591u, 0xe6a2u, 0xf7b3u};
 #pragma unroll
     for (int r = 0; r < LR; ++r) {
         const uint32_t s = prmt_sx(wa[r >> 2], wb[r >> 2], SEL[r & 3]);
-        const uint32_t d = hdiag + s + KD;                 // H(i-1, j-1) + score
-        E[r] = vmax2(Ho[r], madd(E[r], one, nEP));         // E(i, j) from H(i, j-1) - o and E(i, j-1) - e
-        f = vmax2(hup, madd(f, one, nEP));                 // F(i, j) from H(i-1, j) - o and F(i-1, j) - e
-        const uint32_t h = vmax2(vmax2(d, E[r]), vmax2(f, Z));
+        const uint32_t d = __vadd2(hdiag, s);                 // H(i-1, j-1) + score
+        E[r] = __viaddmax_s16x2(E[r], nEP, Ho[r]);            // E(i, j) = max(E(i, j-1) - e, H(i, j-1) - o)
+        f = __viaddmax_s16x2(f, nEP, hup);                    // F(i, j) = max(F(i-1, j) - e, H(i-1, j) - o)
+        const uint32_t h = __vimax3_s16x2_relu(d, E[r], f);   // H = max(0, diagonal, E, F)
         hdiag = Ho[r];
-        Ho[r] = madd(h, one, nOP);
+        Ho[r] = __vsub2(h, OP);
         hup = Ho[r];
-        kA[r] = (uint32_t)max((int)kA[r], (int)prmt(Ho[r], jt, 0x1054u));
-        kB[r] = (uint32_t)max((int)kB[r], (int)prmt(Ho[r], jt, 0x3254u));
+        kA[r] = (uint32_t)max((int)kA[r], (int)madd(Ho[r], sh16, jt));
+        kB[r] = (uint32_t)max((int)kB[r], (int)((Ho[r] & 0xFFFF0000u) | jt));
     }
 }
 
@@ -163,16 +160,16 @@ __device__ void score_pair(const uint8_t *__restrict__ prof, int prow8, const ui
     constexpr int STRIPE = 32 * LR;
     const int lane = threadIdx.x & 31;
     const int n = max(nA, nB);
-    const uint32_t INIT = (uint32_t)(BIAS - o) * P2;       // x = -o in both halves
-    const uint32_t nOP = 0u - (uint32_t)o * P2, nEP = 0u - (uint32_t)e * P2;
-    const uint32_t KD = (uint32_t)(o - BIAS) * P2;         // d = Ho(i-1, j-1) + o + score: bias folded in
+    const uint32_t INIT = ((uint32_t)(-o) & 0xFFFFu) * P2;  // -o in both halves
+    const uint32_t OP = (uint32_t)o * P2, nEP = ((uint32_t)(-e) & 0xFFFFu) * P2;
+    const uint32_t sh16 = one << 16;                        // 2^16 at run time (keeps the multiply-add)
     int bA = -1, iA = 0, jA = 0, bB = -1, iB = 0, jB = 0;
     const int nstripes = (m + STRIPE - 1) / STRIPE;
     for (int stripe = 0; stripe < nstripes; ++stripe) {
         const int row0 = stripe * STRIPE + lane * LR;
         uint32_t Ho[LR], E[LR], kA[LR], kB[LR];
 #pragma unroll
-        for (int r = 0; r < LR; ++r) { Ho[r] = INIT; E[r] = INIT; kA[r] = 0; kB[r] = 0; }
+        for (int r = 0; r < LR; ++r) { Ho[r] = INIT; E[r] = INIT; kA[r] = 0x80000000u; kB[r] = 0x80000000u; }
         uint32_t hd = INIT;                                 // Ho(row0 - 1, j - 1)
         uint32_t out_h = INIT, out_f = INIT, out_t = 0;
         const uint2 *in_buf = buf + (size_t)(stripe & 1) * sstride;
@@ -203,7 +200,7 @@ __device__ void score_pair(const uint8_t *__restrict__ prof, int prow8, const ui
             if (j >= 0 && j < n) {
                 uint32_t f = fu, hup = hu;
                 column2<LR>(pr + (int)(tt & 0xFFFFu) * prow8, pr + (int)(tt >> 16) * prow8, Ho, E, kA, kB, hd, f,
-                            hup, 65535u - (uint32_t)j, one, nOP, nEP, KD);
+                            hup, 65535u - (uint32_t)j, sh16, OP, nEP);
                 hd = hu;
                 out_h = hup; out_f = f; out_t = tt;
                 if (lane == 31 && !last) out_buf[j] = make_uint2(hup, f);
@@ -212,8 +209,8 @@ __device__ void score_pair(const uint8_t *__restrict__ prof, int prow8, const ui
         // this lane's rows: first maximum per pair, and the row-pair bounds
 #pragma unroll
         for (int r = 0; r < LR; r += 2) {
-            const int xa0 = (int)(kA[r] >> 16) - BIAS + o, xa1 = (int)(kA[r + 1] >> 16) - BIAS + o;
-            const int xb0 = (int)(kB[r] >> 16) - BIAS + o, xb1 = (int)(kB[r + 1] >> 16) - BIAS + o;
+            const int xa0 = ((int)kA[r] >> 16) + o, xa1 = ((int)kA[r + 1] >> 16) + o;
+            const int xb0 = ((int)kB[r] >> 16) + o, xb1 = ((int)kB[r + 1] >> 16) + o;
             const int i = row0 + r;
             if (i < m) {
                 bmA[i >> 1] = (int16_t)max(xa0, xa1);
@@ -500,7 +497,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * SW_WARPS + warp;
     uint2 *my = reinterpret_cast<uint2 *>(scratch + (size_t)gw * warp_bytes);
-    const bool packable = o + e <= GAP_MAX;
+    const bool packable = o <= GAP_MAX;
     unsigned long long my_cells = 0;
     for (;;) {
         if (threadIdx.x == 0) { s_seg = atomicAdd(next_seg, 1); s_next = 0; }
@@ -514,16 +511,16 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
         const int m = (int)(qoffsets[qi + 1] - qo);
         const int lr = rows_per_lane(m);
         const int prow8 = ((m + 32 * lr - 1) / (32 * lr)) * STRIPE_BYTES;     // profile bytes per residue
-        // query profile: byte (st * 512 + l * 16 + r) of residue c = M[q_i][c] + BIAS for row
-        // i = st * 32 * lr + l * lr + r of the query; 0 for the pad residue, unused slots
-        // and rows past the query
+        // query profile: byte (st * 512 + l * 16 + r) of residue c = M[q_i][c] + o for row
+        // i = st * 32 * lr + l * lr + r of the query; o - 64 for the pad residue, unused
+        // slots and rows past the query
         if (prow8 <= prow_cap) {
             for (int x = threadIdx.x; x < NRES * prow8; x += blockDim.x) {
                 const int c = x / prow8, rest = x - c * prow8;
                 const int st = rest / STRIPE_BYTES, l = (rest % STRIPE_BYTES) / SLOT, r = rest % SLOT;
                 const int i = st * 32 * lr + l * lr + r;
-                s_prof[x] = (uint8_t)((r < lr && i < m && c < PASTIS_NSYM)
-                                          ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] + BIAS : 0);
+                s_prof[x] = (uint8_t)(int8_t)((r < lr && i < m && c < PASTIS_NSYM)
+                                                  ? (int)gmat[qcodes[qo + i] * PASTIS_NSYM + c] + o : o - 64);
             }
         }
         // the segment's pairs by target length, longest first, so that the two pairs of
