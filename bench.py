@@ -241,9 +241,25 @@ def run_prefilter(args):
     xt, yt = x[take].contiguous(), y[take].contiguous()
     net = F.MLP(seed=11)
     hist = F.train(ctx, net, xt, yt, epochs=3, batch=65536, lr=2e-3, seed=13)
+    n_train = int(xt.shape[0])
     train_s = time.perf_counter() - t0
+    src_desc = w["desc"]
+    cal_rows, eval_from = blocks[1], 2
+    if args.apply:
+        # apply the trained network to a fresh set of another workload (e.g. the exact
+        # k-mer x-drop pipeline of the 1,000,000-protein recipe, seed + 1)
+        del codes, cands, alns, x, y, xt, yt
+        name = args.apply
+        w = WORKLOADS[name]
+        ps = make_set(name, seed_offset=1)
+        a = torch.from_numpy(ps.ascii).to(dev)
+        o = torch.from_numpy(ps.offsets).to(dev)
+        params = P.Params(matrix=synth.blosum62(), k=6, m_subs=w["m"], mode=w["mode"])
+        batches = args.batches or (64 if ps.n >= 500_000 else 16)
+        blocks = row_blocks(ps.n, batches)
+        cal_rows, eval_from = blocks[0], 1
     # calibration block
-    codes, cands, alns, _ = exact(blocks[1])
+    codes, cands, alns, _ = exact(cal_rows)
     yc = F.labels_from(alns)
     zc = F.forward(ctx, net, F.features(ctx, codes, o, cands, params))
     thr = F.threshold_for_recall(zc, yc, args.calib_recall)
@@ -271,7 +287,7 @@ def run_prefilter(args):
         edges = P.filter_edges(ctx, o, kept, alns, params)
         return dict(cands=cands, kept=kept, edges=edges)
 
-    eval_blocks = [blocks[k] for k in range(2, min(batches, 2 + max(args.steps, 1)))]
+    eval_blocks = [blocks[k] for k in range(eval_from, min(batches, eval_from + max(args.steps, 1)))]
     for rows in eval_blocks[:1]:          # warm-up of both forms
         plain(rows)
         prefiltered(rows)
@@ -297,10 +313,11 @@ def run_prefilter(args):
     v_pref = e_pref / t_pref
     line = {"metric": "prefilter speedup vs plain at >= 99.5% edge recall (edges/s ratio)",
             "value": v_pref / v_plain, "unit": "x", "higher_is_better": True, "n_gpus": 1,
-            "steps": len(eval_blocks), "warmup": 1, "dtype": "bf16 (MLP) / int32 (alignment)", "data": "synthetic",
+            "steps": len(eval_blocks), "warmup": 1, "dtype": "bf16 (MLP) / int16x2 + int32 (alignment)", "data": "synthetic",
             "config": {"workload": w["desc"], "name": name, "batch": f"{len(eval_blocks)} of {batches} equal-work row blocks",
-                       "train": f"{xt.shape[0]} labelled candidates of block 0, 3 epochs, Adam 2e-3",
-                       "calibration": f"threshold {thr:.4f} for recall {args.calib_recall} on block 1 "
+                       "train": (f"{n_train} labelled candidates of block 0 of: {src_desc}, 3 epochs, Adam 2e-3"
+                                 + (f"; applied to a fresh set (seed + 1) of {name}" if args.apply else "")),
+                       "calibration": f"threshold {thr:.4f} for recall {args.calib_recall} on one block "
                                       f"(target {args.recall} on the evaluation blocks)"},
             "recall_target_met": None,
             "edges_per_s_plain": v_plain, "edges_per_s_prefiltered": v_pref, "edge_recall": recall,
@@ -409,7 +426,9 @@ def run_serve(args):
     name = args.workload
     w = WORKLOADS[name]
     db = make_set(name)
-    other = make_set(name, seed_offset=100)
+    # unrelated queries: a set of the same recipe with another seed (a 100,000-protein
+    # one for the 1,000,000-protein database)
+    other = make_set(name if db.n <= 100_000 else "zipf_100k_s25_sw", seed_offset=100)
     params = P.Params(matrix=synth.blosum62(), k=6, m_subs=0, mode=w["mode"])
     rng = np.random.default_rng(17)
     sizes = np.exp(rng.uniform(0.0, np.log(4096.0), size=args.requests)).astype(np.int64).clip(1, 4096)
@@ -445,7 +464,8 @@ def run_serve(args):
     srv.close()
     line = {"metric": "serving: query batches vs a resident database (queries/s, p50/p99 latency)",
             "value": st["queries_per_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
-            "steps": len(reqs), "warmup": 3, "dtype": "int32", "data": "synthetic",
+            "steps": len(reqs), "warmup": 3, "data": "synthetic",
+            "dtype": "int16x2 / int32" if w["mode"] == 0 else "int32",
             "config": {"workload": f"database: {w['desc']}; exact k-mers (m = 0)", "name": name,
                        "requests": len(reqs), "request_sizes": "log-uniform 1..4096 queries",
                        "arrivals": f"Poisson, {rate:.3f} requests/s (70% of batch capacity)",
@@ -480,6 +500,8 @@ def main():
     ap.add_argument("--calib-recall", type=float, default=0.998,
                     help="recall the threshold is calibrated for on the calibration block (margin over --recall)")
     ap.add_argument("--train-pairs", type=int, default=10_000_000)
+    ap.add_argument("--apply", default=None, choices=sorted(WORKLOADS),
+                    help="prefilter mode: evaluate the network trained on --workload on a fresh set of this workload")
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
