@@ -131,34 +131,63 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
     res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
 }
 
-// The same extension with the band in registers: lane L holds band cells L and 32 + L
-// of an antidiagonal (band index = a - start of that antidiagonal's computed range),
-// neighbours on the two antidiagonals before come by shuffles, the live range by a
-// ballot and the best cell by two reductions: the largest H, then the smallest a
-// holding it, as above.  Returns false (nothing written) when an antidiagonal
-// needs more than 64 cells; the caller then runs xd_extend_warp.
-constexpr int XD_BAND = 64;
+// The same extension with the cells indexed by diagonal k = a - b instead of by a.  Along
+// an alignment the live cells stay near a few diagonals, so a window of 128 diagonals
+// holds them: lane L owns diagonals kbase + 4L .. kbase + 4L + 3 and keeps each one's
+// latest H, E, F and carries.  Antidiagonal d has cells only on diagonals of d's parity,
+// two per lane; a cell's diagonal predecessor (d-2) is its own diagonal, its E (a, b-1)
+// and F (a-1, b) predecessors (d-1) the diagonals k+1 and k-1: in the lane itself except
+// one, which one shuffle brings from the next or previous lane.  Cells outside the
+// computed range of the definition above are set dead, so the result is the same as
+// xd_extend_warp's.  The window moves by whole lanes when the computed range leaves it;
+// a range wider than XD_BAND cells returns false (nothing written) and the caller runs
+// xd_extend_warp.
+constexpr int XD_BAND = 64;                 // cells of one antidiagonal: 32 lanes x 2
 
-template <typename T>
-__device__ __forceinline__ T xd_get(const T (&X)[2], int idx, bool wide, T none) {
-    const T v0 = __shfl_sync(0xffffffffu, X[0], idx & 31);
-    T v = v0;
-    if (wide) {
-        const T v1 = __shfl_sync(0xffffffffu, X[1], idx & 31);
-        v = idx >= 32 ? v1 : v0;
+struct xd_src { int h, x; uint32_t hc, xc; };   // a predecessor cell: H, E or F, and carries
+
+__device__ __forceinline__ void xd_cell(int a, int b, int d, int clo, int chi, const uint8_t *q, int qs,
+                                        const uint8_t *t, int ts, const int *s_mat, int o, int e, int lim,
+                                        const xd_src &se, const xd_src &sf, int &H, int &E, int &F, uint32_t &HC,
+                                        uint32_t &EC, uint32_t &FC) {
+    int ev = NEG, fv = NEG, h = NEG;
+    uint32_t evc = 0u, fvc = 0u, hc = 0u;
+    if (a >= clo && a <= chi) {
+        if (b >= 1) {
+            const int eo = se.h - o, ex = se.x - e;
+            if (eo >= ex) { ev = eo; evc = se.hc; } else { ev = ex; evc = se.xc; }
+            if (ev < NEG) ev = NEG;
+        }
+        if (a >= 1) {
+            const int fo = sf.h - o, fx = sf.x - e;
+            if (fo >= fx) { fv = fo; fvc = sf.hc; } else { fv = fx; fvc = sf.xc; }
+            if (fv < NEG) fv = NEG;
+        }
+        int dv = NEG;
+        uint32_t dvc = 0u;
+        if (a >= 1 && b >= 1 && H != NEG) {
+            const int qa = q[(long long)(a - 1) * qs], tb = t[(long long)(b - 1) * ts];
+            dv = H + s_mat[qa * 32 + tb];
+            dvc = HC + (qa == tb ? 0x10001u : 1u);
+        }
+        h = dv; hc = dvc;
+        if (fv > h) { h = fv; hc = fvc; }
+        if (ev > h) { h = ev; hc = evc; }
+        if (h < lim) { h = NEG; ev = NEG; fv = NEG; }
     }
-    return (unsigned)idx < (wide ? 64u : 32u) ? v : none;
+    (void)d;
+    H = h; E = ev; F = fv; HC = hc; EC = evc; FC = fvc;
 }
 
-__device__ bool xd_band_warp(const uint8_t *q, int A, int qs, const uint8_t *t, int B, int ts, const int *s_mat,
+__device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, int B, int ts, const int *s_mat,
                              int o, int e, int X, ext_out *res) {
     const int lane = threadIdx.x & 31;
-    // antidiagonal d-1 (start w1, computed width W1) and d-2 (w2, W2); d = 0 is the anchor
-    int H1[2] = {lane == 0 ? 0 : NEG, NEG}, E1[2] = {NEG, NEG}, F1[2] = {NEG, NEG};
-    uint32_t HC1[2] = {0u, 0u}, EC1[2] = {0u, 0u}, FC1[2] = {0u, 0u};
-    int H2[2] = {NEG, NEG};
-    uint32_t HC2[2] = {0u, 0u};
-    int w1 = 0, W1 = 1, w2 = 0, W2 = 0;
+    int H[4], E[4], F[4];
+    uint32_t HC[4], EC[4], FC[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) { H[m] = NEG; E[m] = NEG; F[m] = NEG; HC[m] = 0u; EC[m] = 0u; FC[m] = 0u; }
+    int kbase = -64;                        // diagonal 0 (the anchor) at lane 16, m = 0
+    if (lane == 16) H[0] = 0;
     int best = 0, ba = 0, bb = 0;
     uint32_t bc = 0;
     long long cells = 1;
@@ -167,61 +196,69 @@ __device__ bool xd_band_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
         const int clo = max(max(llo, d - B), 0);
         const int chi = min(min(lhi + 1, A), d);
         if (clo > chi) break;
-        const int W = chi - clo + 1;
-        if (W > XD_BAND) return false;
-        const bool wide = W > 32 || W1 > 32 || W2 > 32;
-        int h[2] = {NEG, NEG}, ev[2] = {NEG, NEG}, fv[2] = {NEG, NEG};
-        uint32_t hc[2] = {0u, 0u}, evc[2] = {0u, 0u}, fvc[2] = {0u, 0u};
-        unsigned live[2] = {0u, 0u};
-        int myh = NEG, mya = 0x7FFFFFFF;             // this lane's best live cell (largest H, smallest a)
-        uint32_t myc = 0u;
+        if (chi - clo + 1 > XD_BAND) return false;
+        // diagonals of the computed range are [2 clo - d, 2 chi - d]; with their E and F
+        // predecessors one further on each side they must lie inside the window
+        const int kmin = 2 * clo - d - 1, kmax = 2 * chi - d + 1;
+        if (kmin < kbase || kmax > kbase + 127) {
+            const int sh = ((kmin + kmax) / 2 - (kbase + 64)) / 4;     // whole lanes, centring the range
+            kbase += 4 * sh;
+            if (kmin < kbase || kmax > kbase + 127) return false;
+            const int src = lane + sh;
+            const bool in = (unsigned)src < 32u;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (c == 1 && !wide) break;
-            const int a = clo + 32 * c + lane, b = d - a;
-            const int i1 = a - w1, i2 = a - 1 - w2;
-            const int h1a = xd_get(H1, i1, wide, NEG), e1a = xd_get(E1, i1, wide, NEG);
-            const uint32_t hc1a = xd_get(HC1, i1, wide, 0u), ec1a = xd_get(EC1, i1, wide, 0u);
-            const int h1u = xd_get(H1, i1 - 1, wide, NEG), f1u = xd_get(F1, i1 - 1, wide, NEG);
-            const uint32_t hc1u = xd_get(HC1, i1 - 1, wide, 0u), fc1u = xd_get(FC1, i1 - 1, wide, 0u);
-            const int h2 = xd_get(H2, i2, wide, NEG);
-            const uint32_t hc2 = xd_get(HC2, i2, wide, 0u);
-            if (a <= chi) {
-                if (b >= 1 && i1 >= 0 && i1 < W1) {
-                    const int eo = h1a - o, ex = e1a - e;
-                    if (eo >= ex) { ev[c] = eo; evc[c] = hc1a; } else { ev[c] = ex; evc[c] = ec1a; }
-                    if (ev[c] < NEG) ev[c] = NEG;
-                }
-                if (a >= 1 && i1 - 1 >= 0 && i1 - 1 < W1) {
-                    const int fo = h1u - o, fx = f1u - e;
-                    if (fo >= fx) { fv[c] = fo; fvc[c] = hc1u; } else { fv[c] = fx; fvc[c] = fc1u; }
-                    if (fv[c] < NEG) fv[c] = NEG;
-                }
-                int dv = NEG;
-                uint32_t dvc = 0u;
-                if (a >= 1 && b >= 1 && i2 >= 0 && i2 < W2 && h2 != NEG) {
-                    const int qa = q[(long long)(a - 1) * qs], tb = t[(long long)(b - 1) * ts];
-                    dv = h2 + s_mat[qa * 32 + tb];
-                    dvc = hc2 + (qa == tb ? 0x10001u : 1u);
-                }
-                int hh = dv;
-                uint32_t hcc = dvc;
-                if (fv[c] > hh) { hh = fv[c]; hcc = fvc[c]; }
-                if (ev[c] > hh) { hh = ev[c]; hcc = evc[c]; }
-                if (hh < best - X) { hh = NEG; ev[c] = NEG; fv[c] = NEG; }
-                h[c] = hh; hc[c] = hcc;
-                if (hh != NEG && hh > myh) { myh = hh; mya = a; myc = hcc; }   // chunk 0 first: smaller a
+            for (int m = 0; m < 4; ++m) {
+                const int h = __shfl_sync(0xffffffffu, H[m], src & 31), ee = __shfl_sync(0xffffffffu, E[m], src & 31);
+                const int ff = __shfl_sync(0xffffffffu, F[m], src & 31);
+                const uint32_t hc = __shfl_sync(0xffffffffu, HC[m], src & 31);
+                const uint32_t ec = __shfl_sync(0xffffffffu, EC[m], src & 31);
+                const uint32_t fc = __shfl_sync(0xffffffffu, FC[m], src & 31);
+                H[m] = in ? h : NEG; E[m] = in ? ee : NEG; F[m] = in ? ff : NEG;
+                HC[m] = in ? hc : 0u; EC[m] = in ? ec : 0u; FC[m] = in ? fc : 0u;
             }
-            live[c] = __ballot_sync(0xffffffffu, h[c] != NEG);
         }
-        cells += W;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            H2[c] = H1[c]; HC2[c] = HC1[c];
-            H1[c] = h[c]; E1[c] = ev[c]; F1[c] = fv[c]; HC1[c] = hc[c]; EC1[c] = evc[c]; FC1[c] = fvc[c];
+        const int lim = best - X;
+        const int k0 = kbase + 4 * lane;       // this lane's first diagonal
+        int h0, h1, a0;
+        uint32_t c0, c1;
+        if ((d & 1) == 0) {
+            // cells on m = 0 and m = 2; F of m = 0 is the previous lane's m = 3
+            xd_src up;
+            up.h = __shfl_up_sync(0xffffffffu, H[3], 1); up.x = __shfl_up_sync(0xffffffffu, F[3], 1);
+            up.hc = __shfl_up_sync(0xffffffffu, HC[3], 1); up.xc = __shfl_up_sync(0xffffffffu, FC[3], 1);
+            if (lane == 0) { up.h = NEG; up.x = NEG; }
+            const xd_src e0{H[1], E[1], HC[1], EC[1]}, e2{H[3], E[3], HC[3], EC[3]};
+            const xd_src f2{H[1], F[1], HC[1], FC[1]};
+            a0 = (d + k0) >> 1;
+            xd_cell(a0, d - a0, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e0, up, H[0], E[0], F[0], HC[0], EC[0],
+                    FC[0]);
+            xd_cell(a0 + 1, d - a0 - 1, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e2, f2, H[2], E[2], F[2], HC[2],
+                    EC[2], FC[2]);
+            h0 = H[0]; h1 = H[2]; c0 = HC[0]; c1 = HC[2];
+        } else {
+            // cells on m = 1 and m = 3; E of m = 3 is the next lane's m = 0
+            xd_src dn;
+            dn.h = __shfl_down_sync(0xffffffffu, H[0], 1); dn.x = __shfl_down_sync(0xffffffffu, E[0], 1);
+            dn.hc = __shfl_down_sync(0xffffffffu, HC[0], 1); dn.xc = __shfl_down_sync(0xffffffffu, EC[0], 1);
+            if (lane == 31) { dn.h = NEG; dn.x = NEG; }
+            const xd_src e1{H[2], E[2], HC[2], EC[2]}, f1{H[0], F[0], HC[0], FC[0]};
+            const xd_src f3{H[2], F[2], HC[2], FC[2]};
+            a0 = (d + k0 + 1) >> 1;
+            xd_cell(a0, d - a0, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e1, f1, H[1], E[1], F[1], HC[1], EC[1],
+                    FC[1]);
+            xd_cell(a0 + 1, d - a0 - 1, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, dn, f3, H[3], E[3], F[3], HC[3],
+                    EC[3], FC[3]);
+            h0 = H[1]; h1 = H[3]; c0 = HC[1]; c1 = HC[3];
         }
-        w2 = w1; W2 = W1; w1 = clo; W1 = W;
-        if (!(live[0] | live[1])) break;
+        cells += chi - clo + 1;
+        const bool l0 = h0 != NEG, l1 = h1 != NEG;
+        const unsigned live = __ballot_sync(0xffffffffu, l0 || l1);
+        if (!live) break;
+        // the lane's best live cell (the smaller a first) and its live range
+        int myh = NEG, mya = 0x7FFFFFFF;
+        uint32_t myc = 0u;
+        if (l0) { myh = h0; mya = a0; myc = c0; }
+        if (l1 && h1 > myh) { myh = h1; mya = a0 + 1; myc = c1; }
         const int toph = __reduce_max_sync(0xffffffffu, myh);
         if (toph > best) {
             const int ta = (int)__reduce_min_sync(0xffffffffu, myh == toph ? (unsigned)mya : 0xFFFFFFFFu);
@@ -229,8 +266,10 @@ __device__ bool xd_band_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
             bc = __shfl_sync(0xffffffffu, myc, __ffs(who) - 1);
             best = toph; ba = ta; bb = d - ta;
         }
-        llo = clo + (live[0] ? __ffs(live[0]) - 1 : 32 + __ffs(live[1]) - 1);
-        lhi = clo + (live[1] ? 63 - __clz(live[1]) : 31 - __clz(live[0]));
+        const int first = __ffs(live) - 1, lastl = 31 - __clz(live);
+        const int lo_here = l0 ? a0 : a0 + 1, hi_here = l1 ? a0 + 1 : a0;
+        llo = __shfl_sync(0xffffffffu, lo_here, first);
+        lhi = __shfl_sync(0xffffffffu, hi_here, lastl);
     }
     res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
     return true;
@@ -269,7 +308,7 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, c
             const uint8_t *qa = left ? qcodes + qo + pi - 1 : qcodes + qo + pi + k;
             const uint8_t *ta = left ? tcodes + to + pj - 1 : tcodes + to + pj + k;
             const int A = left ? pi : lq - pi - k, B = left ? pj : lt - pj - k, st = left ? -1 : 1;
-            if (!xd_band_warp(qa, A, st, ta, B, st, s_mat, o, e, X, &r))
+            if (!xd_diag_warp(qa, A, st, ta, B, st, s_mat, o, e, X, &r))
                 xd_extend_warp(qa, A, st, ta, B, st, s_mat, o, e, X, buf, W, &r);
         }
         if (lane == 0) out[task] = r;
