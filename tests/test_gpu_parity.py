@@ -195,7 +195,7 @@ def _all_pairs(n):
     return c
 
 
-@pytest.mark.parametrize("o,e", [(11, 1), (3, 1), (1, 1)])
+@pytest.mark.parametrize("o,e", [(11, 1), (3, 1), (1, 1), (64, 1), (65, 1), (0, 0), (20, 40)])
 def test_sw_parity_edge_cases(P, ctx, o, e):
     ps = edge_case_set()
     cands = _all_pairs(ps.n)
