@@ -51,6 +51,9 @@ WORKLOADS = {
         "1,000,000 proteins: 100,000 Zipf(1.5, 1-200) families (80%) + 20% singletons, lengths log-normal"
         "(median 300) clipped 50-2000, same mutation recipe; k=6 exact k-mers, min_shared 1, x-drop (X = 49) "
         "from both seeds, BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
+    "zipf_20k_xd": dict(n=20_000, m=0, mode=1, desc=(
+        "20,000 proteins of the 100,000-protein recipe; k=6 exact k-mers, x-drop (X = 49) from both seeds "
+        "(profiling stand-in for the x-drop workloads)")),
     "families_1k_sw": dict(n=1000, m=0, mode=0, desc=(
         "1,000 proteins = 100 families x 10, k=6 exact, SW int32, ANI 30 / cov 70")),
 }
