@@ -607,17 +607,17 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
 // ---------------------------------------------------------------------------------
 // pass 3: carries over the rectangle (or the whole matrix for very large scores)
 // ---------------------------------------------------------------------------------
-constexpr int CR = 8;                  // rows per lane
-constexpr int STRIPE3 = 32 * CR;
+constexpr int CR = 8;                  // rows per lane of the small-rectangle groups and of TRACK
 
 struct stripe3_cell { int32_t h, f; uint32_t hb, fb, hm, fm; };
 
 __device__ __forceinline__ uint32_t pack_rc(int r, int c) { return ((uint32_t)r << 16) | (uint32_t)c; }
 
 // Carries begin (row << 16 | col, of the first column) and identities << 16 | matched
-// columns.  TRACK: also finds the row-major first maximum (for pairs pass 1 skipped);
-// otherwise reports the state at (m-1, n-1).
-template <bool TRACK>
+// columns, with CR rows per lane (a stripe is 32 * CR rows).  TRACK: also finds the
+// row-major first maximum (for pairs pass 1 skipped); otherwise reports the state at
+// (m-1, n-1).
+template <bool TRACK, int CR>
 __device__ void carry_warp(const uint8_t *__restrict__ q, int m, const uint8_t *__restrict__ t, int n,
                            const int *__restrict__ s_mat, int o, int e, stripe3_cell *scratch, int sstride,
                            int *h_out, int *ei_out, int *ej_out, uint32_t *beg_out, uint32_t *im_out) {
@@ -626,9 +626,10 @@ __device__ void carry_warp(const uint8_t *__restrict__ q, int m, const uint8_t *
     uint32_t bbeg = 0, bim = 0;
     int endh = NEG;
     uint32_t endb = 0, endm = 0;
-    const int nstripes = (m + STRIPE3 - 1) / STRIPE3;
+    constexpr int STRIPE = 32 * CR;
+    const int nstripes = (m + STRIPE - 1) / STRIPE;
     for (int stripe = 0; stripe < nstripes; ++stripe) {
-        const int row0 = stripe * STRIPE3 + lane * CR;
+        const int row0 = stripe * STRIPE + lane * CR;
         int qoff[CR], Hc[CR], Ec[CR];
         uint32_t HB[CR], EB[CR], HM[CR], EM[CR];
 #pragma unroll
@@ -889,7 +890,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                 if (lq > 0 && lt > 0) {
                     int h, bi, bj;
                     uint32_t beg, im;
-                    carry_warp<true>(qcodes + qo, lq, tcodes + to, lt, s_mat, o, e, my, sstride, &h, &bi, &bj, &beg, &im);
+                    carry_warp<true, CR>(qcodes + qo, lq, tcodes + to, lt, s_mat, o, e, my, sstride, &h, &bi, &bj, &beg,
+                                         &im);
                     if (h > 0)
                         finish_record(rec, h, bi, bj, (int)(beg >> 16), (int)(beg & 0xFFFF), (int)(im >> 16),
                                       (int)(im & 0xFFFF), lq, lt, ani, cov);
@@ -904,8 +906,20 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                 const int ri = r1.rect_i, rj = r1.rect_j;
                 int h, dummy_i, dummy_j;
                 uint32_t beg, im;
-                carry_warp<false>(qcodes + qo + ri, r1.end_i + 1 - ri, tcodes + to + rj, r1.end_j + 1 - rj, s_mat, o,
-                                  e, my, sstride, &h, &dummy_i, &dummy_j, &beg, &im);
+                // rows per lane from the rectangle's height, so that all 32 lanes have rows
+                const int rows = r1.end_i + 1 - ri;
+                const int ns3 = (rows + 32 * CR - 1) / (32 * CR);
+                const int cr = min(CR, max(2, (((rows + 32 * ns3 - 1) / (32 * ns3)) + 1) & ~1));
+                const uint8_t *cq = qcodes + qo + ri, *ct = tcodes + to + rj;
+                const int cn = r1.end_j + 1 - rj;
+#define PASTIS_CARRY_CASE(C) \
+    case C: carry_warp<false, C>(cq, rows, ct, cn, s_mat, o, e, my, sstride, &h, &dummy_i, &dummy_j, &beg, &im); break;
+                switch (cr) {
+                    PASTIS_CARRY_CASE(2) PASTIS_CARRY_CASE(4) PASTIS_CARRY_CASE(6)
+                    default: carry_warp<false, CR>(cq, rows, ct, cn, s_mat, o, e, my, sstride, &h, &dummy_i, &dummy_j,
+                                                   &beg, &im); break;
+                }
+#undef PASTIS_CARRY_CASE
                 if (h != r1.score && lane == 0) atomicExch(err, 1);
                 finish_record(rec, r1.score, r1.end_i, r1.end_j, ri + (int)(beg >> 16), rj + (int)(beg & 0xFFFF),
                               (int)(im >> 16), (int)(im & 0xFFFF), lq, lt, ani, cov);
