@@ -619,6 +619,7 @@ def main():
         cands_total += res["cands"].shape[0]
     clk = clock.stop()
     prof = ctx.profile_read()
+    stats = ctx.stats()
     ctx.profile(False)
     launches = ctx.launches - launches0
     total_cells = int(cells.item())
@@ -671,6 +672,24 @@ def main():
                 "traffic": None, "kernel": "xd_extend",
                 "peak_note": f"{N_SM} SMs x {INT_LANES_PER_SM} 32-bit lanes x {sm_max:.0f} MHz (derived, not measured)",
                 "ops_per_cell": OPS_PER_CELL, "cells": "computed cells of the x-drop extensions"}
+    # roofline of the overlap product (HBM bound): algorithmic bytes = 16 per left-operand
+    # entry (its code, position and posting-list bounds), 8 per product (the posting
+    # entry gathered), 20 per candidate record written
+    roof_spg = None
+    spg_ms = sum(v[1] for k, v in prof.items() if k.startswith("spgemm"))
+    if spg_ms > 0 and stats["spgemm_products"] > 0:
+        spg_bytes = 16 * stats["spgemm_left_entries"] + 8 * stats["spgemm_products"] + 20 * stats["spgemm_records"]
+        peak_gbs, src = 6800.0, "fallback"
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peak_gbs, src = float(json.load(f)["hbm_gbs"]), "measured"
+        except (OSError, KeyError, ValueError):
+            pass
+        ach = spg_bytes / (spg_ms / 1000.0) / 1e9
+        roof_spg = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s", "frac": ach / peak_gbs,
+                    "traffic": None, "kernel": "spgemm (bound, items, concat)", "peak_source": src,
+                    "products": stats["spgemm_products"], "left_entries": stats["spgemm_left_entries"],
+                    "records": stats["spgemm_records"]}
     sw_block = None
     if w["mode"] == 1 and rank == 0:
         # full SW over one block's candidates (the sample of the x-drop workload's pairs)
@@ -730,7 +749,8 @@ def main():
             "cells_per_step": total_cells // args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": roof, "dominant_kernel": dominant, "kernel_ms_timed_region": kernel_ms,
+            "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant,
+            "kernel_ms_timed_region": kernel_ms,
             "sw_on_block": sw_block,
             "clocks": clk, "cpu_baseline": cpu,
         }

@@ -150,6 +150,12 @@ int64_t pastis_ctx_launch_count(const pastis_ctx *ctx);
  * the bytes written.  Enabling again clears the totals.                             */
 pastis_status pastis_ctx_profile(pastis_ctx *ctx, int enable);
 int32_t pastis_ctx_profile_read(pastis_ctx *ctx, char *buf, int32_t len);
+/* Work counters accumulated while profiling is on (cleared when it is enabled), for the
+ * roofline of the overlap product: h_out[0] = posting entries visited (products),
+ * [1] = left-operand entries whose posting lists were walked, [2] = candidate records
+ * written.  Entries past the third are 0.  Synchronises the stream.                 */
+#define PASTIS_STATS 4
+pastis_status pastis_ctx_stats(pastis_ctx *ctx, int64_t *h_out, int32_t n);
 
 /* ---- a1: encode (Sec. V-B) ---------------------------------------------------- */
 

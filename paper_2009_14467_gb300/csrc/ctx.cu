@@ -95,9 +95,28 @@ void prof_end(pastis_ctx *c) {
 extern "C" pastis_status pastis_ctx_profile(pastis_ctx *ctx, int enable) {
     if (!ctx) return PASTIS_ERR_INVALID_ARG;
     prof_flush(ctx);
-    if (enable) { ctx->prof_names = 0; }
+    if (enable) {
+        ctx->prof_names = 0;
+        if (!ctx->d_stats && cudaMalloc(&ctx->d_stats, PASTIS_STATS * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->d_stats = nullptr;
+            return PASTIS_ERR_OUT_OF_MEMORY;
+        }
+        PASTIS_CUDA_TRY(cudaMemsetAsync(ctx->d_stats, 0, PASTIS_STATS * sizeof(unsigned long long), ctx->stream));
+    }
     ctx->prof_on = enable ? 1 : 0;
     ctx->prof_open = 0;
+    return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_ctx_stats(pastis_ctx *ctx, int64_t *h_out, int32_t n) {
+    if (!ctx || !h_out || n < 0) return PASTIS_ERR_INVALID_ARG;
+    unsigned long long v[PASTIS_STATS] = {0, 0, 0, 0};
+    if (ctx->d_stats) {
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(v, ctx->d_stats, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+        PASTIS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    for (int x = 0; x < n; ++x) h_out[x] = x < PASTIS_STATS ? (int64_t)v[x] : 0;
     return PASTIS_OK;
 }
 
@@ -122,6 +141,7 @@ extern "C" pastis_status pastis_ctx_destroy(pastis_ctx *ctx) {
     prof_flush(ctx);
     for (int s = 0; s < WS_COUNT; ++s)
         if (ctx->ws[s]) cudaFree(ctx->ws[s]);
+    if (ctx->d_stats) cudaFree(ctx->d_stats);
     free(ctx);
     return PASTIS_OK;
 }

@@ -52,6 +52,7 @@ struct pastis_ctx {
     int64_t filt_n;
     // profiling: pending event pairs and per-name totals
     int prof_on;
+    unsigned long long *d_stats;   // work counters while profiling: see pastis_ctx_stats
     int prof_open;
     int prof_n;
     prof_rec prof[PASTIS_PROF_MAX];

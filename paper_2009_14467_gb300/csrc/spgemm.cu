@@ -91,16 +91,18 @@ __device__ __forceinline__ int64_t lower_bound_seq(const int32_t *seq, int64_t a
 template <bool TWO>
 __device__ void insert_side(const operand &L, int32_t i, int32_t j0, int32_t j1, int32_t *s_key,
                             uint32_t *s_cnt, unsigned long long *s_s0, unsigned long long *s_s1, int tsize,
-                            int *s_overflow) {
+                            int *s_overflow, unsigned long long &n_left, unsigned long long &n_prod) {
     const int64_t rb = L.row_ptr[i], re = L.row_ptr[i + 1];
     for (int64_t t = rb + threadIdx.x; t < re; t += blockDim.x) {
         const uint32_t c = L.row_code[t];
         const int64_t pb = L.col_ptr[c], pe = L.col_ptr[c + 1];
         int64_t x = lower_bound_seq(L.col_seq, pb, pe, j0);
         const unsigned long long tv = (unsigned long long)(t - rb) << 16;
+        ++n_left;
         for (; x < pe; ++x) {
             const int32_t j = L.col_seq[x];
             if (j >= j1) break;
+            ++n_prod;
             uint32_t slot = hash_j(j) & (uint32_t)(tsize - 1);
             int probes = 0;
             for (;;) {
@@ -142,7 +144,7 @@ template <bool SUBS>
 __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_items(operand F, operand B, const work_item *items,
                                                               int tsize, int32_t min_shared,
                                                               pastis_cand *tmp_out, int64_t *item_count,
-                                                              int *item_overflow) {
+                                                              int *item_overflow, unsigned long long *stats) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *s_s0 = (unsigned long long *)smem;
     unsigned long long *s_s1 = s_s0 + tsize;
@@ -166,8 +168,9 @@ __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_items(operand F, operand
     }
     if (threadIdx.x == 0) { s_overflow = 0; s_nvalid = 0; }
     __syncthreads();
-    insert_side<SUBS>(F, it.i, it.j0, it.j1, s_key, s_cnt, s_s0, s_s1, tsize, &s_overflow);
-    if (SUBS) insert_side<SUBS>(B, it.i, it.j0, it.j1, s_key, s_cntb, s_b0, s_b1, tsize, &s_overflow);
+    unsigned long long n_left = 0, n_prod = 0;
+    insert_side<SUBS>(F, it.i, it.j0, it.j1, s_key, s_cnt, s_s0, s_s1, tsize, &s_overflow, n_left, n_prod);
+    if (SUBS) insert_side<SUBS>(B, it.i, it.j0, it.j1, s_key, s_cntb, s_b0, s_b1, tsize, &s_overflow, n_left, n_prod);
     __syncthreads();
     if (s_overflow) {
         if (threadIdx.x == 0) { item_overflow[blockIdx.x] = 1; item_count[blockIdx.x] = 0; }
@@ -220,6 +223,17 @@ __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_items(operand F, operand
         tmp_out[it.out_off + r] = rec;
     }
     if (threadIdx.x == 0) item_count[blockIdx.x] = nv;
+    if (stats) {                     // work of the items that completed (profiling only)
+        for (int x = 16; x > 0; x >>= 1) {
+            n_left += __shfl_xor_sync(0xffffffffu, n_left, x);
+            n_prod += __shfl_xor_sync(0xffffffffu, n_prod, x);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&stats[0], n_prod);
+            atomicAdd(&stats[1], n_left);
+            if (threadIdx.x == 0) atomicAdd(&stats[2], (unsigned long long)nv);
+        }
+    }
 }
 
 __global__ void k_concat(const pastis_cand *tmp, const work_item *items, const int64_t *item_count,
@@ -402,10 +416,12 @@ static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const p
                 prof_begin(ctx, "spgemm_items");
                 if (subs)
                     k_spgemm_items<true><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
-                        F, Bop, d_items + g0, tsize, params->min_shared, tmp, d_cnt + g0, d_ovf + g0);
+                        F, Bop, d_items + g0, tsize, params->min_shared, tmp, d_cnt + g0, d_ovf + g0,
+                        ctx->prof_on ? ctx->d_stats : nullptr);
                 else
                     k_spgemm_items<false><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
-                        F, Bop, d_items + g0, tsize, params->min_shared, tmp, d_cnt + g0, d_ovf + g0);
+                        F, Bop, d_items + g0, tsize, params->min_shared, tmp, d_cnt + g0, d_ovf + g0,
+                        ctx->prof_on ? ctx->d_stats : nullptr);
                 PASTIS_LAUNCHED(ctx);
                 prof_end(ctx);
             }

@@ -122,6 +122,8 @@ def lib():
             L.pastis_ctx_profile.restype = ctypes.c_int32
             L.pastis_ctx_profile_read.argtypes = [P, ctypes.c_char_p, ctypes.c_int32]
             L.pastis_ctx_profile_read.restype = ctypes.c_int32
+            L.pastis_ctx_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.c_int32]
+            L.pastis_ctx_stats.restype = ctypes.c_int32
             _lib = L
     return _lib
 
@@ -179,6 +181,12 @@ class Context:
             name, cnt, ms = ln.split()
             out[name] = (int(cnt), float(ms))
         return out
+
+    def stats(self) -> dict:
+        """pastis_ctx_stats: overlap-product work counted while profiling was on."""
+        v = (ctypes.c_int64 * 4)()
+        _check("pastis_ctx_stats", lib().pastis_ctx_stats(self.h, v, 4))
+        return {"spgemm_products": v[0], "spgemm_left_entries": v[1], "spgemm_records": v[2]}
 
 
 @dataclass

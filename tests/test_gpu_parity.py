@@ -281,14 +281,21 @@ def test_filter_and_end_to_end(P, ctx):
 def test_profiler_counts_kernels(P, ctx):
     ps = synth.families_1k().subset(np.arange(200))
     params = P.Params(matrix=MAT)
-    for _ in range(2):
+    for it in range(2):
         ctx.profile(True)
-        P.run(ctx, dev(ps.ascii), dev(ps.offsets), params)
+        r = P.run(ctx, dev(ps.ascii), dev(ps.offsets), params)
         prof = ctx.profile_read()
+        st = ctx.stats()
         ctx.profile(False)
         for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_items", "sw_pass1", "sw_pass3",
                      "filter_flags"):
             assert name in prof and prof[name][0] >= 1 and prof[name][1] >= 0.0, name
+        if it == 0:
+            # the overlap product's work counters: one record per candidate, and at least
+            # one product (posting entry) behind each unit of a record's count
+            assert st["spgemm_records"] == r["cands"].shape[0]
+            assert st["spgemm_products"] >= int(P.to_records(r["cands"], P.CAND_DTYPE)["count"].sum())
+            assert st["spgemm_left_entries"] > 0
 
 
 def test_spgemm_row_blocks_concatenate(P, ctx):
