@@ -454,6 +454,29 @@ def run_variants(args):
 # ---------------------------------------------------------------------------------
 # serving: query batches against a resident database
 # ---------------------------------------------------------------------------------
+def train_prefilter_net(P, F, ctx, dev, name, train_pairs, batches=16):
+    """The prefilter network trained on pass/fail labels of the exact path over row
+    block 0 of a set of the given workload (the same recipe as --mode prefilter)."""
+    import torch
+    w = WORKLOADS[name]
+    ps = make_set(name)
+    params = P.Params(matrix=synth.blosum62(), k=6, m_subs=w["m"], mode=w["mode"])
+    a = torch.from_numpy(ps.ascii).to(dev)
+    o = torch.from_numpy(ps.offsets).to(dev)
+    t0 = time.perf_counter()
+    codes = P.encode(ctx, a)
+    A = P.build_kmers(ctx, codes, o, 6)
+    cands = P.overlap_spgemm(ctx, A, params, rows=row_blocks(ps.n, batches)[0])
+    alns = P.align_pairs(ctx, codes, o, cands, params)
+    y = F.labels_from(alns)
+    x = F.features(ctx, codes, o, cands, params)
+    g = torch.Generator(device=dev).manual_seed(7)
+    take = torch.randperm(x.shape[0], device=dev, generator=g)[:min(x.shape[0], train_pairs)]
+    net = F.MLP(seed=11)
+    hist = F.train(ctx, net, x[take].contiguous(), y[take].contiguous(), epochs=3, batch=65536, lr=2e-3, seed=13)
+    return net, int(take.numel()), hist, time.perf_counter() - t0
+
+
 def run_serve(args):
     """Database = the workload's protein set (exact k-mers, resident on the device).
     Requests of log-uniform 1..4096 queries (half drawn from the database's families,
@@ -476,6 +499,28 @@ def run_serve(args):
     for r, sz in enumerate(sizes):
         src = db if r % 2 == 0 else other
         reqs.append(src.subset(rng.choice(src.n, size=int(sz), replace=False)))
+    pref = None
+    if args.prefilter:
+        # network trained on the 100k set's exact run; threshold calibrated for the recall
+        # target on a separate batch of queries against this database
+        from paper_2009_14467_gb300 import prefilter as F
+        ctx = P.Context(0)
+        net, n_train, hist, train_s = train_prefilter_net(P, F, ctx, torch.device("cuda", 0), "zipf_100k_s25_sw",
+                                                          args.train_pairs)
+        crng = np.random.default_rng(29)      # its own stream: the request stream stays the same
+        cal = synth.from_strings([db.seq(int(i)) for i in crng.choice(db.n, 750, replace=False)] +
+                                 [other.seq(int(i)) for i in crng.choice(other.n, 750, replace=False)])
+        srv0 = S.Server(db.ascii, db.offsets, params, slots=1, reserve_bytes=8 << 30)
+        cc = P.encode(ctx, torch.from_numpy(cal.ascii).cuda())
+        co = torch.from_numpy(cal.offsets).cuda()
+        cands = S.query_overlap(ctx, P.build_kmers(ctx, cc, co, 6), srv0.DB, params)
+        alns = S.align_pairs_qt(ctx, cc, co, srv0.db_codes, srv0.db_offsets, cands, params)
+        z = F.forward(ctx, net, F.features_qt(ctx, cc, co, srv0.db_codes, srv0.db_offsets, cands, params))
+        thr = F.threshold_for_recall(z, F.labels_from(alns), args.calib_recall)
+        srv0.close()
+        ctx.close()
+        pref = {"net": net, "threshold": thr, "train_pairs": n_train, "train_s": train_s,
+                "calibration": f"threshold {thr:.4f} for recall {args.calib_recall} on 1,500 calibration queries"}
     srv = S.Server(db.ascii, db.offsets, params, slots=args.slots, reserve_bytes=8 << 30)
     # warm-up, then the batch path: every request in turn on one slot, nothing overlapping
     for q in reqs[:3]:
@@ -499,9 +544,42 @@ def run_serve(args):
     for q, g in zip(reqs, gaps):
         time.sleep(g)
         handles.append(srv.submit(q.ascii, q.offsets))
-    n_edges = sum(len(h.future.result(timeout=3600)) for h in handles)
+    res_plain = [h.future.result(timeout=3600) for h in handles]
+    n_edges = sum(len(r) for r in res_plain)
     st = srv.latency_stats()
     srv.close()
+    pf = None
+    if pref is not None:
+        # the same stream through the prefilter: latency, throughput and edge recall
+        srv = S.Server(db.ascii, db.offsets, params, slots=args.slots, reserve_bytes=8 << 30,
+                       prefilter=(pref["net"], pref["threshold"]))
+        for q in reqs[:3]:
+            srv.submit(q.ascii, q.offsets).future.result()
+        ctx = P.Context(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in reqs:
+            srv.process(ctx, S.Request(q.ascii, q.offsets, 0))
+        torch.cuda.synchronize()
+        cap_pf = nq / (time.perf_counter() - t0)
+        ctx.close()
+        srv.done.clear()
+        handles = []
+        for q, g in zip(reqs, gaps):
+            time.sleep(g)
+            handles.append(srv.submit(q.ascii, q.offsets))
+        res_pf = [h.future.result(timeout=3600) for h in handles]
+        st_pf = srv.latency_stats()
+        srv.close()
+        kept = sum(len(r) for r in res_pf)
+        outside = 0
+        for a, x in zip(res_pf, res_plain):
+            ex = set(zip(x["i"].tolist(), x["j"].tolist()))
+            outside += sum(1 for i, j in zip(a["i"].tolist(), a["j"].tolist()) if (i, j) not in ex)
+        pf = {"queries_per_s": st_pf["queries_per_s"], "p50_s": st_pf["p50_s"], "p99_s": st_pf["p99_s"],
+              "batch_path_queries_per_s": cap_pf, "edges": kept, "edge_recall": kept / max(1, n_edges),
+              "edges_not_in_exact": outside, "train_pairs": pref["train_pairs"], "train_s": pref["train_s"],
+              "calibration": pref["calibration"]}
     line = {"metric": "serving: query batches vs a resident database (queries/s, p50/p99 latency)",
             "value": st["queries_per_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
             "steps": len(reqs), "warmup": 3, "data": "synthetic",
@@ -511,7 +589,8 @@ def run_serve(args):
                        "arrivals": f"Poisson, {rate:.3f} requests/s (70% of batch capacity)",
                        "slots": args.slots},
             "p50_s": st["p50_s"], "p99_s": st["p99_s"], "queries": nq,
-            "batch_path_queries_per_s": cap, "edges": n_edges, "edges_batch_path": n_edges_batch}
+            "batch_path_queries_per_s": cap, "edges": n_edges, "edges_batch_path": n_edges_batch,
+            "prefiltered": pf}
     print(json.dumps(line), flush=True)
     return 0 if n_edges == n_edges_batch else 1
 
@@ -536,6 +615,8 @@ def main():
                          "serve: query batches against a resident database; variants: components, CK, NS")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests in the stream")
     ap.add_argument("--slots", type=int, default=4, help="serve mode: concurrent worker slots")
+    ap.add_argument("--prefilter", action="store_true",
+                    help="serve mode: also run the stream through the learned prefilter")
     ap.add_argument("--recall", type=float, default=0.995, help="edge recall the prefilter must keep")
     ap.add_argument("--calib-recall", type=float, default=0.998,
                     help="recall the threshold is calibrated for on the calibration block (margin over --recall)")

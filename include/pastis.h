@@ -283,6 +283,12 @@ typedef struct pastis_mlp {
 pastis_status pastis_pair_features(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets,
                                    const pastis_cand *d_pairs, int64_t n_pairs,
                                    const pastis_params *params, void *d_x);
+
+/* The same with the queries' and targets' residues in separate arrays (serving form:
+ * pair (i, j) is query i against target j). */
+pastis_status pastis_pair_features_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                      const uint8_t *d_tcodes, const int64_t *d_toffsets, const pastis_cand *d_pairs,
+                                      int64_t n_pairs, const pastis_params *params, void *d_x);
 /* Logits d_logits[n] of d_x[n * 16] (bf16).  Does not synchronise. */
 pastis_status pastis_mlp_forward(pastis_ctx *ctx, const pastis_mlp *net, const void *d_x, int64_t n,
                                  float *d_logits);

@@ -28,13 +28,14 @@ __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162f
 // ---------------------------------------------------------------------------------
 // features
 // ---------------------------------------------------------------------------------
-__global__ void k_pair_features(const uint8_t *codes, const int64_t *offsets, const pastis_cand *pairs, int64_t n,
-                                int k, const int8_t *gmat, __nv_bfloat16 *x) {
+__global__ void k_pair_features(const uint8_t *qcodes, const int64_t *qoffsets, const uint8_t *tcodes,
+                                const int64_t *toffsets, const pastis_cand *pairs, int64_t n, int k,
+                                const int8_t *gmat, __nv_bfloat16 *x) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const pastis_cand c = pairs[p];
-    const int64_t qo = offsets[c.i], to = offsets[c.j];
-    const float lq = (float)(offsets[c.i + 1] - qo), lt = (float)(offsets[c.j + 1] - to);
+    const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
+    const float lq = (float)(qoffsets[c.i + 1] - qo), lt = (float)(toffsets[c.j + 1] - to);
     float f[FEAT];
 #pragma unroll
     for (int t = 0; t < FEAT; ++t) f[t] = 0.f;
@@ -43,8 +44,8 @@ __global__ void k_pair_features(const uint8_t *codes, const int64_t *offsets, co
     const float d1 = two ? (float)c.qpos[1] - (float)c.tpos[1] : d0;
     float s0 = 0.f, s1 = 0.f;
     for (int t = 0; t < k; ++t) {
-        s0 += gmat[codes[qo + c.qpos[0] + t] * PASTIS_NSYM + codes[to + c.tpos[0] + t]];
-        if (two) s1 += gmat[codes[qo + c.qpos[1] + t] * PASTIS_NSYM + codes[to + c.tpos[1] + t]];
+        s0 += gmat[qcodes[qo + c.qpos[0] + t] * PASTIS_NSYM + tcodes[to + c.tpos[0] + t]];
+        if (two) s1 += gmat[qcodes[qo + c.qpos[1] + t] * PASTIS_NSYM + tcodes[to + c.tpos[1] + t]];
     }
     const float mn = fminf(lq, lt), mx = fmaxf(lq, lt);
     f[0] = log1pf((float)c.count);
@@ -256,23 +257,36 @@ pastis_status gemm(pastis_ctx *ctx, const __nv_bfloat16 *A, const __nv_bfloat16 
 
 }  // namespace
 
-extern "C" pastis_status pastis_pair_features(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets,
-                                              const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *params,
-                                              void *d_x) {
+static pastis_status features_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                 const uint8_t *d_tcodes, const int64_t *d_toffsets, const pastis_cand *d_pairs,
+                                 int64_t n_pairs, const pastis_params *params, void *d_x) {
     if (!ctx || n_pairs < 0) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
     if (n_pairs == 0) return PASTIS_OK;
-    if (!d_codes || !d_offsets || !d_pairs || !d_x) return PASTIS_ERR_INVALID_ARG;
+    if (!d_qcodes || !d_qoffsets || !d_tcodes || !d_toffsets || !d_pairs || !d_x) return PASTIS_ERR_INVALID_ARG;
     int8_t *dmat;
     PASTIS_WS(dmat, ctx, WS_FLAGS, 1024);
     PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, params->matrix, 576, cudaMemcpyHostToDevice, ctx->stream));
     prof_begin(ctx, "mlp_features");
     k_pair_features<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, ctx->stream>>>(
-        d_codes, d_offsets, d_pairs, n_pairs, params->k, dmat, (__nv_bfloat16 *)d_x);
+        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat, (__nv_bfloat16 *)d_x);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_pair_features(pastis_ctx *ctx, const uint8_t *d_codes, const int64_t *d_offsets,
+                                              const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *params,
+                                              void *d_x) {
+    return features_qt(ctx, d_codes, d_offsets, d_codes, d_offsets, d_pairs, n_pairs, params, d_x);
+}
+
+extern "C" pastis_status pastis_pair_features_qt(pastis_ctx *ctx, const uint8_t *d_qcodes,
+                                                 const int64_t *d_qoffsets, const uint8_t *d_tcodes,
+                                                 const int64_t *d_toffsets, const pastis_cand *d_pairs,
+                                                 int64_t n_pairs, const pastis_params *params, void *d_x) {
+    return features_qt(ctx, d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params, d_x);
 }
 
 // Scratch activations for n rows: h1, h2 (bf16 n x 256), z (f32 n), and for training

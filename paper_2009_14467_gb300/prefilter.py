@@ -32,6 +32,8 @@ def _lib():
         P, i64 = ctypes.c_void_p, ctypes.c_int64
         L.pastis_pair_features.argtypes = [P, P, P, P, i64, ctypes.POINTER(_p.c_params), P]
         L.pastis_pair_features.restype = ctypes.c_int32
+        L.pastis_pair_features_qt.argtypes = [P, P, P, P, P, P, i64, ctypes.POINTER(_p.c_params), P]
+        L.pastis_pair_features_qt.restype = ctypes.c_int32
         L.pastis_mlp_forward.argtypes = [P, ctypes.POINTER(c_mlp), P, i64, P]
         L.pastis_mlp_forward.restype = ctypes.c_int32
         L.pastis_mlp_train_step.argtypes = [P, ctypes.POINTER(c_mlp), P, P, i64, ctypes.c_float, ctypes.c_float, P]
@@ -100,6 +102,17 @@ def features(ctx, codes, offsets, pairs, params) -> torch.Tensor:
     p = params.c()
     _p._check("pastis_pair_features", _lib().pastis_pair_features(
         ctx.h, _p._ptr(codes), _p._ptr(offsets), _p._ptr(pairs), n, ctypes.byref(p), _p._ptr(x)))
+    return x[:n]
+
+
+def features_qt(ctx, qcodes, qoffsets, tcodes, toffsets, pairs, params) -> torch.Tensor:
+    """Features of query x target candidates (serving form)."""
+    n = pairs.shape[0]
+    x = torch.empty((max(n, 1), FEAT), dtype=torch.bfloat16, device=qcodes.device)
+    p = params.c()
+    _p._check("pastis_pair_features_qt", _lib().pastis_pair_features_qt(
+        ctx.h, _p._ptr(qcodes), _p._ptr(qoffsets), _p._ptr(tcodes), _p._ptr(toffsets), _p._ptr(pairs), n,
+        ctypes.byref(p), _p._ptr(x)))
     return x[:n]
 
 

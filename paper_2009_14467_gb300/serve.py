@@ -8,7 +8,7 @@ context, take the next request as soon as they are free and the device has room 
 it (admission by free device memory), so requests that arrive while others run are
 admitted as slots and memory free up, and their kernels overlap on the GPU.  Each
 request runs the hot path in serving form: encode -> query k-mer matrix -> query x
-database candidates -> alignment -> filter, and
+database candidates -> (optional learned prefilter) -> alignment -> filter, and
 returns the edges (query index, database index, ident, cols, score, ANI).  Every
 numeric step is a library kernel; this module only schedules.
 """
@@ -44,10 +44,11 @@ class Server:
     """Query batches against a resident database."""
 
     def __init__(self, db_ascii: np.ndarray, db_offsets: np.ndarray, params: P.Params, device: int = 0,
-                 slots: int = 4, reserve_bytes: int = 8 << 30):
+                 slots: int = 4, reserve_bytes: int = 8 << 30, prefilter=None):
         if params.m_subs != 0:
             raise ValueError("the serving form takes exact k-mers (m_subs = 0)")
         self.params = params
+        self.prefilter = prefilter          # (prefilter.MLP, threshold) or None
         self.device = torch.device("cuda", device)
         self.reserve = reserve_bytes
         torch.cuda.set_device(self.device)
@@ -105,6 +106,11 @@ class Server:
         codes = P.encode(ctx, a)
         Q = P.build_kmers(ctx, codes, o, self.params.k)
         cands = query_overlap(ctx, Q, self.DB, self.params)
+        if self.prefilter is not None and cands.shape[0] > 0:
+            from . import prefilter as F
+            net, thr = self.prefilter
+            z = F.forward(ctx, net, F.features_qt(ctx, codes, o, self.db_codes, self.db_offsets, cands, self.params))
+            cands = F.select(ctx, cands, z, thr)
         alns = align_pairs_qt(ctx, codes, o, self.db_codes, self.db_offsets, cands, self.params)
         edges = filter_edges_qt(ctx, o, self.db_offsets, cands, alns, self.params)
         return P.to_records(edges, P.EDGE_DTYPE)

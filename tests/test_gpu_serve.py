@@ -60,3 +60,57 @@ def test_serving_matches_oracle_alone_and_in_the_mix(server):
         assert a.tobytes() == m.tobytes()
     st = srv.latency_stats()
     assert st["requests"] >= 2 * len(reqs) and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_features_qt_equal_features_of_the_joined_set(server):
+    P, srv, db, reqs = server
+    from paper_2009_14467_gb300 import pastis as PP, prefilter as F
+    q = reqs[3]
+    ctx = PP.Context(0)
+    codes_q = PP.encode(ctx, torch.from_numpy(q.ascii).cuda())
+    oq = torch.from_numpy(q.offsets).cuda()
+    Q = PP.build_kmers(ctx, codes_q, oq, 6)
+    from paper_2009_14467_gb300 import serve as S
+    cands = S.query_overlap(ctx, Q, srv.DB, srv.params)
+    x_qt = F.features_qt(ctx, codes_q, oq, srv.db_codes, srv.db_offsets, cands, srv.params)
+    both = synth.from_strings([q.seq(i) for i in range(q.n)] + [db.seq(j) for j in range(db.n)])
+    codes_b = PP.encode(ctx, torch.from_numpy(both.ascii).cuda())
+    rec = PP.to_records(cands, PP.CAND_DTYPE)
+    rec["j"] += q.n
+    x_b = F.features(ctx, codes_b, torch.from_numpy(both.offsets).cuda(),
+                     torch.from_numpy(rec.view(np.uint8).reshape(-1, 20)).cuda(), srv.params)
+    assert cands.shape[0] > 0 and torch.equal(x_qt.view(torch.int16), x_b.view(torch.int16))
+    ctx.close()
+
+
+def test_serving_with_prefilter_alone_equals_mixed(server):
+    P, srv, db, reqs = server
+    from paper_2009_14467_gb300 import pastis as PP, prefilter as F, serve as S
+    net = F.MLP(seed=3)
+    # threshold: the median logit over one request's candidates (keeps about half)
+    ctx = PP.Context(0)
+    q = reqs[5]
+    codes = PP.encode(ctx, torch.from_numpy(q.ascii).cuda())
+    o = torch.from_numpy(q.offsets).cuda()
+    cands = S.query_overlap(ctx, PP.build_kmers(ctx, codes, o, 6), srv.DB, srv.params)
+    z = F.forward(ctx, net, F.features_qt(ctx, codes, o, srv.db_codes, srv.db_offsets, cands, srv.params))
+    thr = float(z.median().item())
+    ctx.close()
+    pf = S.Server(db.ascii, db.offsets, srv.params, slots=3, reserve_bytes=1 << 30, prefilter=(net, thr))
+    try:
+        alone = [pf.submit(q.ascii, q.offsets, r).future.result(timeout=120) for r, q in enumerate(reqs)]
+        handles = [pf.submit(q.ascii, q.offsets, 100 + r) for r, q in enumerate(reqs)]
+        mixed = [h.future.result(timeout=300) for h in handles]
+    finally:
+        pf.close()
+    exact = [srv.submit(q.ascii, q.offsets, 200 + r).future.result(timeout=120) for r, q in enumerate(reqs)]
+    kept = total = 0
+    for a, m, x in zip(alone, mixed, exact):
+        assert a.tobytes() == m.tobytes()
+        ex = {(int(i), int(j)): k for k, (i, j) in enumerate(zip(x["i"], x["j"]))}
+        for rec in a:
+            assert (int(rec["i"]), int(rec["j"])) in ex            # prefiltered edges are exact edges
+            assert rec.tobytes() == x[ex[(int(rec["i"]), int(rec["j"]))]].tobytes()
+        kept += len(a)
+        total += len(x)
+    assert 0 < kept <= total
