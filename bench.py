@@ -609,6 +609,8 @@ def main():
     ap.add_argument("--batches", type=int, default=None,
                     help="equal-work query-row blocks the job is split into (default: 8 for 100k sets, else 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-1 layout (no tuner)")
+    ap.add_argument("--tune-pairs", type=int, default=3_000_000, help="candidates the tuner samples")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
     ap.add_argument("--mode", default="plain", choices=["plain", "prefilter", "serve", "variants"],
                     help="plain: the exact path (the headline); prefilter: learned prefilter vs plain; "
@@ -670,6 +672,27 @@ def main():
         rows = blocks[counter[0] % batches]
         counter[0] += 1
         return P.run(ctx, ascii_dev, offs_dev, params, cells, rows=rows)
+
+    tune = None
+    if w["mode"] != 1 and not args.no_autotune:
+        # setup, untimed: the pass-1 layout per query-length bin, tuned on the candidates
+        # of every stride-th query of block 0
+        t0 = time.perf_counter()
+        codes = P.encode(ctx, ascii_dev)
+        A = P.build_kmers(ctx, codes, offs_dev, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=blocks[0])
+        stride = max(1, -(-cands.shape[0] // args.tune_pairs))
+        qi = cands.view(torch.int32).view(-1, 5)[:, 0]
+        sample = cands[(qi % stride) == 0].contiguous()
+        extra, cyc = P.autotune_sw(ctx, codes, offs_dev, sample, params, reps=2)
+        torch.cuda.synchronize()
+        base = float(cyc[0].sum())
+        chosen = float(sum(cyc[extra[b], b] for b in range(P.pastis.SW_BINS)))
+        tune = {"sample_pairs": int(sample.shape[0]), "sample": f"candidates of every {stride}th query of block 0",
+                "setup_s": round(time.perf_counter() - t0, 2), "bins_changed": int((extra > 0).sum()),
+                "layout": {f"{32 * b + 1}-{32 * b + 32}": int(extra[b]) for b in np.flatnonzero(extra)},
+                "pass1_cycles_saved_on_sample": round(1.0 - chosen / base, 4) if base > 0 else 0.0}
+        del codes, A, cands, qi, sample
 
     for _ in range(args.warmup):
         res = step()
@@ -832,7 +855,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant,
             "kernel_ms_timed_region": kernel_ms,
-            "sw_on_block": sw_block,
+            "sw_on_block": sw_block, "autotune": tune,
             "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -152,7 +152,8 @@ pastis_status pastis_ctx_profile(pastis_ctx *ctx, int enable);
 int32_t pastis_ctx_profile_read(pastis_ctx *ctx, char *buf, int32_t len);
 /* Work counters accumulated while profiling is on (cleared when it is enabled), for the
  * roofline of the overlap product: h_out[0] = posting entries visited (products),
- * [1] = left-operand entries whose posting lists were walked, [2] = candidate records
+ * [1] = left-operand entries of the rows formed, each counted once per row even when
+ * the row is split into column ranges that walk it again, [2] = candidate records
  * written.  Entries past the third are 0.  Synchronises the stream.                 */
 #define PASTIS_STATS 4
 pastis_status pastis_ctx_stats(pastis_ctx *ctx, int64_t *h_out, int32_t n);
@@ -251,6 +252,39 @@ pastis_status pastis_align_pairs_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, co
                                     int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
                                     int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
                                     const pastis_params *params, pastis_aln *d_out, int64_t *d_cells);
+
+/* ---- batching: the Smith-Waterman tile layout and its tuner -----------------------
+ * Pass 1 of PASTIS_SW / PASTIS_SW_SCORE computes a query of m residues in stripes of
+ * 32 lanes x LR rows (LR even, 2..16).  By default it takes as few stripes as 16 rows
+ * per lane allow; a layout adds, per query-length bin (bin = (m-1) / 32, the last bin
+ * taking every longer query), 0..PASTIS_SW_MAX_EXTRA stripes, which pads fewer rows
+ * but sweeps the target more often.  The layout is a speed choice only: every output
+ * of every entry point is the same under every layout.                             */
+#define PASTIS_SW_BINS 64
+#define PASTIS_SW_BIN_WIDTH 32
+#define PASTIS_SW_MAX_EXTRA 2
+
+/* Sets the context's layout from h_extra[PASTIS_SW_BINS] (host; NULL = the default,
+ * all 0).  A value above PASTIS_SW_MAX_EXTRA gives PASTIS_ERR_INVALID_ARG and leaves
+ * the layout unchanged.  pastis_sw_layout_get copies the current one to h_extra.     */
+pastis_status pastis_sw_layout_set(pastis_ctx *ctx, const uint8_t *h_extra);
+pastis_status pastis_sw_layout_get(const pastis_ctx *ctx, uint8_t *h_extra);
+
+/* The autotuner: runs pass 1 over the given pairs (the arguments of
+ * pastis_align_pairs_qt; a sample of the workload's candidates) once per uniform
+ * layout 0..PASTIS_SW_MAX_EXTRA, `reps` times each, with the SM cycles of every
+ * query's work summed per length bin; each bin takes the layout with the fewest cycles
+ * when it beats the default by at least 2%, else the default.  The chosen layout is
+ * set on the context and copied to h_extra (optional, PASTIS_SW_BINS bytes); h_cycles
+ * (optional, host, PASTIS_SW_BINS * (PASTIS_SW_MAX_EXTRA + 1) int64, [x * BINS + bin])
+ * receives the measured cycles.  params->mode must be PASTIS_SW or PASTIS_SW_SCORE
+ * (PASTIS_ERR_UNSUPPORTED otherwise).  Validation and errors as
+ * pastis_align_pairs_qt; the layout is unchanged on error.  Synchronises.           */
+pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                 int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                 int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
+                                 const pastis_params *params, int32_t reps, uint8_t *h_extra,
+                                 int64_t *h_cycles);
 
 /* ---- a10: similarity filter (Sec. IV-F, VI-B) ----------------------------------- */
 

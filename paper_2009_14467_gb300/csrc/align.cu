@@ -9,6 +9,7 @@
 // (identities << 16 | matched columns) along the predecessor a traceback would take
 // (diagonal > F > E, open > extend), so the end cell holds the path's statistics.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -409,7 +410,12 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     PASTIS_WS(dmat, ctx, WS_FLAGS, 1024);
     int *flags = (int *)(dmat + 768);   // [0] error, [1] [3] [8] pair counters, [2] max length, [4] bad pair,
                                         // [5] bad code, [6..7] task counter
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, params->matrix, 576, cudaMemcpyHostToDevice, st));
+    // the matrix, then the pass-1 layout at dmat + 640
+    uint8_t hconst[640 + PASTIS_SW_BINS];
+    memcpy(hconst, params->matrix, 576);
+    memset(hconst + 576, 0, 64);
+    memcpy(hconst + 640, ctx->sw_lay.extra, PASTIS_SW_BINS);
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, hconst, sizeof(hconst), cudaMemcpyHostToDevice, st));
     PASTIS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64, st));
     const int xd = params->mode == PASTIS_XD;
     k_max_len<<<(unsigned)ceil_div64(n_q, 256), 256, 0, st>>>(d_qoffsets, n_q, flags + 2);
@@ -489,4 +495,77 @@ extern "C" pastis_status pastis_align_pairs_qt(pastis_ctx *ctx, const uint8_t *d
                                                const pastis_params *params, pastis_aln *d_out, int64_t *d_cells) {
     return align_qt(ctx, d_qcodes, d_qoffsets, n_q, d_tcodes, d_toffsets, n_t, d_pairs, n_pairs, params, d_out,
                     d_cells);
+}
+
+extern "C" pastis_status pastis_sw_layout_set(pastis_ctx *ctx, const uint8_t *h_extra) {
+    if (!ctx) return PASTIS_ERR_INVALID_ARG;
+    sw_layout lay;
+    for (int b = 0; b < PASTIS_SW_BINS; ++b) {
+        const int v = h_extra ? h_extra[b] : 0;
+        if (v > PASTIS_SW_MAX_EXTRA) return PASTIS_ERR_INVALID_ARG;
+        lay.extra[b] = (uint8_t)v;
+    }
+    ctx->sw_lay = lay;
+    return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_sw_layout_get(const pastis_ctx *ctx, uint8_t *h_extra) {
+    if (!ctx || !h_extra) return PASTIS_ERR_INVALID_ARG;
+    for (int b = 0; b < PASTIS_SW_BINS; ++b) h_extra[b] = ctx->sw_lay.extra[b];
+    return PASTIS_OK;
+}
+
+// Pass 1 under each uniform layout (score mode: pass 1 and the score-only records), the
+// per-bin cycles of each run summed over reps; per bin the fastest layout when it beats
+// the default by 2% or more.
+extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                            int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                            int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
+                                            const pastis_params *params, int32_t reps, uint8_t *h_extra,
+                                            int64_t *h_cycles) {
+    if (!ctx || !params || reps < 1 || n_pairs < 0) return PASTIS_ERR_INVALID_ARG;
+    pastis_status s = check_params(params);
+    if (s != PASTIS_OK) return s;
+    if (params->mode != PASTIS_SW && params->mode != PASTIS_SW_SCORE) return PASTIS_ERR_UNSUPPORTED;
+    constexpr int NX = PASTIS_SW_MAX_EXTRA + 1;
+    const sw_layout saved = ctx->sw_lay;
+    int64_t cyc[NX * PASTIS_SW_BINS] = {0};
+    if (n_pairs > 0) {
+        unsigned long long *d_tune;
+        PASTIS_WS(d_tune, ctx, WS_TUNE, sizeof(unsigned long long) * NX * PASTIS_SW_BINS +
+                                            sizeof(pastis_aln) * (size_t)n_pairs + 16);
+        pastis_aln *d_out = (pastis_aln *)(d_tune + NX * PASTIS_SW_BINS);
+        PASTIS_CUDA_TRY(cudaMemsetAsync(d_tune, 0, sizeof(unsigned long long) * NX * PASTIS_SW_BINS, ctx->stream));
+        pastis_params ps = *params;
+        ps.mode = PASTIS_SW_SCORE;
+        for (int r = 0; r < reps && s == PASTIS_OK; ++r) {
+            for (int x = 0; x < NX && s == PASTIS_OK; ++x) {
+                for (int b = 0; b < PASTIS_SW_BINS; ++b) ctx->sw_lay.extra[b] = (uint8_t)x;
+                ctx->d_tune = d_tune + x * PASTIS_SW_BINS;
+                s = align_qt(ctx, d_qcodes, d_qoffsets, n_q, d_tcodes, d_toffsets, n_t, d_pairs, n_pairs, &ps, d_out,
+                             nullptr);
+            }
+        }
+        ctx->d_tune = nullptr;
+        ctx->sw_lay = saved;
+        if (s != PASTIS_OK) return s;
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(cyc, d_tune, sizeof(cyc), cudaMemcpyDeviceToHost, ctx->stream));
+        PASTIS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    sw_layout best;
+    for (int b = 0; b < PASTIS_SW_BINS; ++b) {
+        int bx = 0;
+        for (int x = 1; x < NX; ++x)
+            if (cyc[x * PASTIS_SW_BINS + b] > 0 && cyc[x * PASTIS_SW_BINS + b] < cyc[bx * PASTIS_SW_BINS + b])
+                bx = x;
+        // keep the default unless the winner is clearly faster
+        if (bx != 0 && (double)cyc[bx * PASTIS_SW_BINS + b] > 0.98 * (double)cyc[b]) bx = 0;
+        best.extra[b] = (uint8_t)bx;
+    }
+    ctx->sw_lay = best;
+    if (h_extra)
+        for (int b = 0; b < PASTIS_SW_BINS; ++b) h_extra[b] = best.extra[b];
+    if (h_cycles)
+        for (int x = 0; x < NX * PASTIS_SW_BINS; ++x) h_cycles[x] = cyc[x];
+    return PASTIS_OK;
 }

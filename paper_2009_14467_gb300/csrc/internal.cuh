@@ -22,8 +22,16 @@ enum ws_slot {
     WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER, WS_ALN_BOUND, WS_ALN_BOFF,
     WS_FILT_FLAGS, WS_FILT_SCAN, WS_CC,
     WS_MLP,
+    WS_TUNE,
     WS_COUNT
 };
+
+// Pass-1 stripe layout per query-length bin (set by pastis_sw_layout_set or the tuner).
+struct sw_layout { uint8_t extra[PASTIS_SW_BINS]; };
+__host__ __device__ static inline int sw_bin(int m) {
+    const int b = (m - 1) / PASTIS_SW_BIN_WIDTH;
+    return b < 0 ? 0 : (b >= PASTIS_SW_BINS ? PASTIS_SW_BINS - 1 : b);
+}
 
 // Per-kernel CUDA-event timing (enabled by pastis_ctx_profile).
 struct prof_rec {
@@ -53,6 +61,8 @@ struct pastis_ctx {
     // profiling: pending event pairs and per-name totals
     int prof_on;
     unsigned long long *d_stats;   // work counters while profiling: see pastis_ctx_stats
+    sw_layout sw_lay;              // pass-1 stripe layout per query-length bin
+    unsigned long long *d_tune;    // per-bin pass-1 cycles while the tuner runs, else null
     int prof_open;
     int prof_n;
     prof_rec prof[PASTIS_PROF_MAX];

@@ -53,7 +53,7 @@ struct operand {          // one side of the product: left rows and right postin
 struct work_item {
     int32_t i;
     int32_t j0, j1;       // column range [j0, j1)
-    int32_t pad;
+    int32_t first;        // 1 when j0 is the row's first column (its left entries are counted there)
     int64_t out_off;      // slice in the temporary record buffer
     int64_t out_cap;
 };
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_items(operand F, operand
         }
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(&stats[0], n_prod);
-            atomicAdd(&stats[1], n_left);
+            if (it.first) atomicAdd(&stats[1], n_left);   // each left entry once per row
             if (threadIdx.x == 0) atomicAdd(&stats[2], (unsigned long long)nv);
         }
     }
@@ -393,7 +393,8 @@ static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const p
         std::vector<work_item> wi((size_t)ni);
         int64_t off = 0;
         for (int64_t x = 0; x < ni; ++x) {
-            wi[x].i = pending[x].i; wi[x].j0 = pending[x].j0; wi[x].j1 = pending[x].j1; wi[x].pad = 0;
+            wi[x].i = pending[x].i; wi[x].j0 = pending[x].j0; wi[x].j1 = pending[x].j1;
+            wi[x].first = pending[x].j0 == (self ? pending[x].i + 1 : 0);
             wi[x].out_off = off; wi[x].out_cap = pending[x].cap;
             off += pending[x].cap;
         }

@@ -100,10 +100,12 @@ __device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t c) {
 
 struct end_cell { int h, i, j; };
 
-// Rows per lane: as few stripes as 16 rows per lane allow, then the smallest even row
-// count that covers the query in that many stripes.
-__device__ __forceinline__ int rows_per_lane(int m) {
-    const int ns = max(1, (m + 511) / 512);
+// Rows per lane: as few stripes as 16 rows per lane allow, plus `extra` stripes (the
+// layout the tuner picked for the query's length bin), then the smallest even row count
+// that covers the query in that many stripes.  More stripes pad fewer rows but sweep the
+// target more often; the layout changes no result.
+__device__ __forceinline__ int rows_per_lane(int m, int extra) {
+    const int ns = max(1, (m + 511) / 512) + extra;
     const int per = (m + 32 * ns - 1) / (32 * ns);
     return min(16, max(2, (per + 1) & ~1));
 }
@@ -489,7 +491,8 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                                                          int max_s, int prow_cap, uint32_t one, char *scratch,
                                                          size_t warp_bytes, int sstride, int *next_seg,
                                                          int16_t *bm_all, const int64_t *bm_off, sw_score_out *out,
-                                                         unsigned long long *cells) {
+                                                         unsigned long long *cells, const uint8_t *extra,
+                                                         unsigned long long *tune) {
     // dynamic shared memory: the profile [NRES][prow_cap] bytes (prow_cap a whole number of stripes)
     extern __shared__ __align__(16) uint8_t s_prof[];
     __shared__ int s_seg, s_next;
@@ -504,13 +507,20 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
         __syncthreads();
         const int64_t sg = s_seg;
         if (sg >= n_seg) break;
+        const long long t_seg = tune ? clock64() : 0;
         const int64_t p0 = seg_start[sg], p1 = seg_start[sg + 1];
         const int cnt = (int)(p1 - p0);
         const int qi = pairs[p0].i;
         const int64_t qo = qoffsets[qi];
         const int m = (int)(qoffsets[qi + 1] - qo);
-        const int lr = rows_per_lane(m);
-        const int prow8 = ((m + 32 * lr - 1) / (32 * lr)) * STRIPE_BYTES;     // profile bytes per residue
+        const int bin = sw_bin(m);
+        const int ex = extra[bin];
+        int lr = rows_per_lane(m, ex);
+        int prow8 = ((m + 32 * lr - 1) / (32 * lr)) * STRIPE_BYTES;     // profile bytes per residue
+        if (prow8 > prow_cap && ex) {                                  // the extra stripes do not fit
+            lr = rows_per_lane(m, 0);
+            prow8 = ((m + 32 * lr - 1) / (32 * lr)) * STRIPE_BYTES;
+        }
         // query profile: byte (st * 512 + l * 16 + r) of residue c = M[q_i][c] + o for row
         // i = st * 32 * lr + l * lr + r of the query; o - 64 for the pad residue, unused
         // slots and rows past the query
@@ -600,6 +610,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
             }
         }
         __syncthreads();
+        if (tune && threadIdx.x == 0) atomicAdd(&tune[bin], (unsigned long long)(clock64() - t_seg));
     }
     if (lane == 0 && cells && my_cells) atomicAdd(cells, my_cells);
 }
@@ -980,7 +991,9 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     sw_score_out *res;
     PASTIS_WS(res, ctx, WS_ALN_PASS1, sizeof(sw_score_out) * (size_t)n_pairs);
     // pass 1+2: profile rows up to the longest query (in whole stripes), within shared memory
-    int prow_cap = ((lmax + STRIPE1 - 1) / STRIPE1) * STRIPE1;
+    int max_extra = 0;
+    for (int b = 0; b < PASTIS_SW_BINS; ++b) max_extra = std::max(max_extra, (int)ctx->sw_lay.extra[b]);
+    int prow_cap = ((lmax + STRIPE1 - 1) / STRIPE1 + max_extra) * STRIPE1;
     if (prow_cap < STRIPE1) prow_cap = STRIPE1;
     auto shm_for = [](int pc) { return (size_t)NRES * pc; };
     while (prow_cap > STRIPE1 && shm_for(prow_cap) + 1024 > ctx->smem_optin) prow_cap -= STRIPE1;
@@ -1001,7 +1014,8 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
                                                   (int64_t)h_nseg, dmat,
                                                   p->gap_open, p->gap_extend, max_s, prow_cap, 1u, (char *)scratch,
                                                   warp_bytes, sstride, flags + 1, bm_all, bm_off, res,
-                                                  (unsigned long long *)d_cells);
+                                                  (unsigned long long *)d_cells, (const uint8_t *)dmat + 640,
+                                                  ctx->d_tune);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     const int score_only = p->mode == PASTIS_SW_SCORE;

@@ -17,6 +17,7 @@ from . import build as _build
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 SW, XD, SW_SCORE = 0, 1, 2
+SW_BINS, SW_BIN_WIDTH, SW_MAX_EXTRA = 64, 32, 2     # pass-1 layout per query-length bin
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_RESIDUE", 3: "CAPACITY", 4: "OUT_OF_MEMORY",
           5: "CUDA", 6: "TIMEOUT", 7: "UNSUPPORTED", 8: "INTERNAL"}
@@ -188,6 +189,24 @@ class Context:
         _check("pastis_ctx_stats", lib().pastis_ctx_stats(self.h, v, 4))
         return {"spgemm_products": v[0], "spgemm_left_entries": v[1], "spgemm_records": v[2]}
 
+    def sw_layout(self) -> np.ndarray:
+        """pastis_sw_layout_get: extra pass-1 stripes per query-length bin (uint8[64])."""
+        _layout_sigs()
+        out = np.zeros(SW_BINS, np.uint8)
+        _check("pastis_sw_layout_get", lib().pastis_sw_layout_get(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_sw_layout(self, extra=None):
+        """pastis_sw_layout_set (None: the default layout)."""
+        _layout_sigs()
+        if extra is None:
+            _check("pastis_sw_layout_set", lib().pastis_sw_layout_set(self.h, None))
+            return
+        a = np.ascontiguousarray(extra, dtype=np.uint8)
+        if a.shape != (SW_BINS,):
+            raise ValueError(f"a layout has {SW_BINS} entries")
+        _check("pastis_sw_layout_set", lib().pastis_sw_layout_set(self.h, a.ctypes.data_as(ctypes.c_void_p)))
+
 
 @dataclass
 class KMat:
@@ -291,6 +310,39 @@ def align_pairs(ctx: Context, codes: torch.Tensor, offsets: torch.Tensor, pairs:
                                                           _ptr(pairs), n, ctypes.byref(p), _ptr(out),
                                                           _ptr(cells)))
     return out[:n]
+
+
+def _layout_sigs():
+    L = lib()
+    if not getattr(L, "_layout_sigs", False):
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.pastis_sw_layout_set.argtypes = [P, P]
+        L.pastis_sw_layout_set.restype = i32
+        L.pastis_sw_layout_get.argtypes = [P, P]
+        L.pastis_sw_layout_get.restype = i32
+        L.pastis_autotune_sw.argtypes = [P, P, P, i32, P, P, i32, P, i64, ctypes.POINTER(c_params), i32, P, P]
+        L.pastis_autotune_sw.restype = i32
+        L._layout_sigs = True
+    return L
+
+
+def autotune_sw(ctx: Context, codes: torch.Tensor, offsets: torch.Tensor, pairs: torch.Tensor, params: Params,
+                reps: int = 2, tcodes: torch.Tensor = None, toffsets: torch.Tensor = None):
+    """pastis_autotune_sw over the given pairs (targets in codes/offsets unless tcodes/
+    toffsets are given).  Sets the chosen layout on ctx and returns (layout uint8[64],
+    cycles int64[3, 64])."""
+    L = _layout_sigs()
+    tcodes = codes if tcodes is None else tcodes
+    toffsets = offsets if toffsets is None else toffsets
+    extra = np.zeros(SW_BINS, np.uint8)
+    cyc = np.zeros((SW_MAX_EXTRA + 1, SW_BINS), np.int64)
+    p = params.c()
+    _check("pastis_autotune_sw", L.pastis_autotune_sw(ctx.h, _ptr(codes), _ptr(offsets), offsets.numel() - 1,
+                                                      _ptr(tcodes), _ptr(toffsets), toffsets.numel() - 1,
+                                                      _ptr(pairs), pairs.shape[0], ctypes.byref(p), reps,
+                                                      extra.ctypes.data_as(ctypes.c_void_p),
+                                                      cyc.ctypes.data_as(ctypes.c_void_p)))
+    return extra, cyc
 
 
 def filter_edges(ctx: Context, offsets: torch.Tensor, pairs: torch.Tensor, alns: torch.Tensor,

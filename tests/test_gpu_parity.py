@@ -295,7 +295,10 @@ def test_profiler_counts_kernels(P, ctx):
             # one product (posting entry) behind each unit of a record's count
             assert st["spgemm_records"] == r["cands"].shape[0]
             assert st["spgemm_products"] >= int(P.to_records(r["cands"], P.CAND_DTYPE)["count"].sum())
-            assert st["spgemm_left_entries"] > 0
+            # each left-operand entry once: the entries of the rows of A (exact k-mers,
+            # every row but the last forms products over j > i)
+            row_ptr, _, _ = O.kmers(O.encode(ps.ascii), ps.offsets, 6)
+            assert st["spgemm_left_entries"] == int(row_ptr[-2])
 
 
 def test_spgemm_row_blocks_concatenate(P, ctx):
