@@ -791,7 +791,7 @@ def main():
             pass
         ach = spg_bytes / (spg_ms / 1000.0) / 1e9
         roof_spg = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s", "frac": ach / peak_gbs,
-                    "traffic": None, "kernel": "spgemm (bound, items, concat)", "peak_source": src,
+                    "traffic": None, "kernel": "spgemm (cursors, rows, concat)", "peak_source": src,
                     "products": stats["spgemm_products"], "left_entries": stats["spgemm_left_entries"],
                     "records": stats["spgemm_records"]}
     sw_block = None

@@ -8,18 +8,24 @@
 // (AS)_i . A_j and A_i . (AS)_j, and each pair keeps the orientation that shares more
 // (i -> j on ties).
 //
-// Row-wise hash SpGEMM.  A work item is a row i and a column range [J0, J1) of j > i.
-// One CTA owns an item and a hash table in shared memory keyed by j; each left entry
-// (k-mer t of row i) walks its posting list (sorted by sequence, so the range start is
-// found by binary search) and for every j inserts: count += 1 and the seed
-// t << 16 | pos_j into a two-smallest pair with the atomicMin swap
-//     old = atomicMin(s0, v);  atomicMin(s1, max(old, v))
-// which leaves s0, s1 = the two smallest values whatever the arrival order.  Row
-// entries are in ascending code order, so the smallest t is the smallest code.  The
-// CTA then compacts the entries that pass min_shared, sorts them by j (bitonic), and
-// writes records to a per-item slice; a final pass concatenates the slices in (i, j)
-// order.  Rows whose product bound exceeds a table are split into column ranges by
-// the host; a range that still overflows is flagged and split again.
+// Row-wise hash SpGEMM in two kernels.
+//  * Cursors: one warp per row i.  Each left entry t of the row (a k-mer of AS_i, and of
+//    A_i for the second orientation) finds where its posting list (sorted by sequence)
+//    reaches the row's first column j >= jlo; entries with a non-empty rest keep a
+//    cursor (next j, posting index, posting end).  The warp also sums the row's exact
+//    product count.
+//  * Rows: one CTA per row, a hash table in shared memory keyed by j (count and two
+//    seeds per orientation).  A row whose products could overflow the table is formed
+//    in column ranges [a, z), in order; each range advances every cursor up to z, so
+//    each posting entry is visited once however many ranges the row takes.  An entry
+//    inserts count += 1 and the seed t << 16 | pos_j into a two-smallest pair with
+//        old = atomicMin(s0, v);  atomicMin(s1, max(old, v))
+//    which leaves s0, s1 = the two smallest values whatever the arrival order.  Row
+//    entries are in ascending code order, so the smallest t is the smallest code.  After
+//    each range the CTA compacts the entries that pass min_shared, sorts them by j
+//    (bitonic) and appends their records to the row's slice; a table that overflows
+//    (more distinct j than it holds) resets the cursors to the range start and halves
+//    the range.  A final pass concatenates the slices in row order.
 #include <algorithm>
 #include <vector>
 
@@ -39,7 +45,10 @@ pastis_status build_as(pastis_ctx *ctx, const pastis_kmat *A, const pastis_param
 namespace {
 
 constexpr int SPG_THREADS = 256;
+constexpr int CUR_THREADS = 256;
 constexpr uint64_t SEED_NONE = ~0ull;
+constexpr int32_t J_DONE = 0x7FFFFFFF;     // cursor past its posting list
+constexpr uint32_t SIDE_B = 0x80000000u;   // cursor of the second orientation
 
 struct operand {          // one side of the product: left rows and right posting lists
     const int64_t *row_ptr;
@@ -50,27 +59,21 @@ struct operand {          // one side of the product: left rows and right postin
     const uint16_t *col_pos;
 };
 
-struct work_item {
+struct cursors {          // per kept left entry of the rows of one call
+    int32_t *nj;          // next column j of the entry (J_DONE when exhausted)
+    uint32_t *t;          // entry index within its row | SIDE_B
+    int64_t *x;           // posting index of nj
+    int64_t *pe;          // end of the posting list
+};
+
+struct row_item {
     int32_t i;
-    int32_t j0, j1;       // column range [j0, j1)
-    int32_t first;        // 1 when j0 is the row's first column (its left entries are counted there)
+    int32_t pieces;       // column ranges the row starts with
+    int64_t ent_off;      // first cursor of the row
+    int64_t n_act;        // cursors of the row
     int64_t out_off;      // slice in the temporary record buffer
     int64_t out_cap;
 };
-
-// Upper bound of the products of row i over j > i: posting lengths of its entries.
-__global__ void k_row_bound(operand L, int32_t n, int64_t *bound) {
-    int32_t i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;
-    int64_t acc = 0;
-    for (int64_t t = L.row_ptr[i] + lane; t < L.row_ptr[i + 1]; t += 32) {
-        uint32_t c = L.row_code[t];
-        acc += (int64_t)(L.col_ptr[c + 1] - L.col_ptr[c]);
-    }
-    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-    if (lane == 0) bound[i] = acc;
-}
 
 __device__ __forceinline__ uint32_t hash_j(int32_t j) { return (uint32_t)j * 2654435761u; }
 
@@ -87,34 +90,56 @@ __device__ __forceinline__ int64_t lower_bound_seq(const int32_t *seq, int64_t a
     return a;
 }
 
-// Inserts every product of one orientation into the table.  Returns false on overflow.
-template <bool TWO>
-__device__ void insert_side(const operand &L, int32_t i, int32_t j0, int32_t j1, int32_t *s_key,
-                            uint32_t *s_cnt, unsigned long long *s_s0, unsigned long long *s_s1, int tsize,
-                            int *s_overflow, unsigned long long &n_left, unsigned long long &n_prod) {
-    const int64_t rb = L.row_ptr[i], re = L.row_ptr[i + 1];
-    for (int64_t t = rb + threadIdx.x; t < re; t += blockDim.x) {
-        const uint32_t c = L.row_code[t];
-        const int64_t pb = L.col_ptr[c], pe = L.col_ptr[c + 1];
-        int64_t x = lower_bound_seq(L.col_seq, pb, pe, j0);
-        const unsigned long long tv = (unsigned long long)(t - rb) << 16;
-        ++n_left;
-        for (; x < pe; ++x) {
-            const int32_t j = L.col_seq[x];
-            if (j >= j1) break;
-            ++n_prod;
-            uint32_t slot = hash_j(j) & (uint32_t)(tsize - 1);
-            int probes = 0;
-            for (;;) {
-                int32_t prev = atomicCAS(&s_key[slot], -1, j);
-                if (prev == -1 || prev == j) break;
-                slot = (slot + 1) & (uint32_t)(tsize - 1);
-                if (++probes >= tsize) { *s_overflow = 1; return; }
+// Cursors of the rows rows[w] (one warp each): entries with postings at j >= jlo, in
+// entry order (first orientation, then the second), their count and the row's products.
+__global__ void __launch_bounds__(CUR_THREADS) k_spgemm_cursors(operand F, operand B, int subs, int self,
+                                                               const int32_t *rows, const int64_t *ent_off,
+                                                               int32_t n_rows, cursors cur, int64_t *n_act,
+                                                               int64_t *n_prod, unsigned long long *stats) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_rows) return;
+    const int32_t i = rows[w];
+    const int32_t jlo = self ? i + 1 : 0;
+    const int64_t base = ent_off[w];
+    int64_t cnt = 0, prod = 0, left = 0;
+    for (int side = 0; side <= subs; ++side) {
+        const operand &L = side ? B : F;
+        const int64_t rb = L.row_ptr[i], re = L.row_ptr[i + 1];
+        left += re - rb;
+        for (int64_t t0 = rb; t0 < re; t0 += 32) {
+            const int64_t t = t0 + lane;
+            bool act = false;
+            int64_t x = 0, pe = 0;
+            int32_t nj = 0;
+            if (t < re) {
+                const uint32_t c = L.row_code[t];
+                const int64_t pb = L.col_ptr[c];
+                pe = L.col_ptr[c + 1];
+                if (pe > pb) {
+                    x = lower_bound_seq(L.col_seq, pb, pe, jlo);
+                    if (x < pe) { act = true; nj = L.col_seq[x]; }
+                }
             }
-            atomicAdd(&s_cnt[slot], 1u);
-            const unsigned long long v = tv | (unsigned long long)L.col_pos[x];
-            const unsigned long long old = atomicMin(&s_s0[slot], v);
-            atomicMin(&s_s1[slot], old > v ? old : v);
+            const unsigned m = __ballot_sync(0xffffffffu, act);
+            if (act) {
+                const int64_t pos = base + cnt + __popc(m & ((1u << lane) - 1u));
+                cur.nj[pos] = nj;
+                cur.t[pos] = (uint32_t)(t - rb) | (side ? SIDE_B : 0u);
+                cur.x[pos] = x;
+                cur.pe[pos] = pe;
+                prod += pe - x;
+            }
+            cnt += __popc(m);
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) prod += __shfl_down_sync(0xffffffffu, prod, d);
+    if (lane == 0) {
+        n_act[w] = cnt;
+        n_prod[w] = prod;
+        if (stats) {
+            atomicAdd(&stats[0], (unsigned long long)prod);
+            atomicAdd(&stats[1], (unsigned long long)left);
         }
     }
 }
@@ -137,14 +162,14 @@ __device__ void bitonic_sort_pairs(uint32_t *key, uint32_t *val, int n) {
     }
 }
 
-// One CTA per work item.  SUBS: two orientations per entry (fwd = (AS)_i A_j,
-// bwd = A_i (AS)_j).  Shared memory: key[T], cnt[T], s0[T], s1[T] (+ cnt_b, s0_b, s1_b),
-// then sort scratch key[T], val[T].
+// One CTA per row (items of one table size).  SUBS: two orientations per entry
+// (fwd = (AS)_i A_j, bwd = A_i (AS)_j).  Shared memory: s0[T], s1[T] (+ b0[T], b1[T]),
+// key[T], cnt[T] (+ cnt_b[T]), then sort scratch key[T], val[T].
 template <bool SUBS>
-__global__ void __launch_bounds__(SPG_THREADS) k_spgemm_items(operand F, operand B, const work_item *items,
-                                                              int tsize, int32_t min_shared,
-                                                              pastis_cand *tmp_out, int64_t *item_count,
-                                                              int *item_overflow, unsigned long long *stats) {
+__global__ void __launch_bounds__(SPG_THREADS) k_spgemm_rows(operand F, operand B, const row_item *items,
+                                                             int tsize, int32_t min_shared, int self, int32_t n_cols,
+                                                             cursors cur, pastis_cand *tmp_out, int64_t *item_count,
+                                                             int *item_error, unsigned long long *stats) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *s_s0 = (unsigned long long *)smem;
     unsigned long long *s_s1 = s_s0 + tsize;
@@ -158,92 +183,151 @@ __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_items(operand F, operand
     __shared__ int s_overflow;
     __shared__ int s_nvalid;
 
-    const work_item it = items[blockIdx.x];
-    for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
-        s_key[x] = -1;
-        s_cnt[x] = 0;
-        s_s0[x] = SEED_NONE;
-        s_s1[x] = SEED_NONE;
-        if (SUBS) { s_cntb[x] = 0; s_b0[x] = SEED_NONE; s_b1[x] = SEED_NONE; }
-    }
-    if (threadIdx.x == 0) { s_overflow = 0; s_nvalid = 0; }
-    __syncthreads();
-    unsigned long long n_left = 0, n_prod = 0;
-    insert_side<SUBS>(F, it.i, it.j0, it.j1, s_key, s_cnt, s_s0, s_s1, tsize, &s_overflow, n_left, n_prod);
-    if (SUBS) insert_side<SUBS>(B, it.i, it.j0, it.j1, s_key, s_cntb, s_b0, s_b1, tsize, &s_overflow, n_left, n_prod);
-    __syncthreads();
-    if (s_overflow) {
-        if (threadIdx.x == 0) { item_overflow[blockIdx.x] = 1; item_count[blockIdx.x] = 0; }
-        return;
-    }
-    // compact passing entries
-    for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
-        if (s_key[x] < 0) continue;
-        uint32_t c = s_cnt[x];
-        if (SUBS && s_cntb[x] > c) c = s_cntb[x];
-        if ((int64_t)c < (int64_t)min_shared) continue;
-        int r = atomicAdd(&s_nvalid, 1);
-        s_sk[r] = (uint32_t)s_key[x];
-        s_sv[r] = (uint32_t)x;
-    }
-    __syncthreads();
-    const int nv = s_nvalid;
-    int np2 = 1;
-    while (np2 < nv) np2 <<= 1;
-    for (int x = nv + threadIdx.x; x < np2; x += blockDim.x) { s_sk[x] = 0xFFFFFFFFu; s_sv[x] = 0; }
-    __syncthreads();
-    bitonic_sort_pairs(s_sk, s_sv, np2);
-    if (nv > it.out_cap) {   // cannot happen with the capacities the planner sets
-        if (threadIdx.x == 0) { item_overflow[blockIdx.x] = 1; item_count[blockIdx.x] = 0; }
-        return;
-    }
-    const int64_t rb_f = F.row_ptr[it.i];
-    const int64_t rb_b = SUBS ? B.row_ptr[it.i] : 0;
-    for (int r = threadIdx.x; r < nv; r += blockDim.x) {
-        const int slot = (int)s_sv[r];
-        pastis_cand rec;
-        rec.i = it.i;
-        rec.j = (int32_t)s_sk[r];
-        bool use_b = SUBS && (s_cntb[slot] > s_cnt[slot]);
-        unsigned long long sd[2];
-        int64_t rb;
-        const uint16_t *lpos;
-        if (use_b) {
-            rec.count = s_cntb[slot]; sd[0] = s_b0[slot]; sd[1] = s_b1[slot]; rb = rb_b; lpos = B.row_pos;
-        } else {
-            rec.count = s_cnt[slot]; sd[0] = s_s0[slot]; sd[1] = s_s1[slot]; rb = rb_f; lpos = F.row_pos;
+    const row_item it = items[blockIdx.x];
+    const int32_t i = it.i;
+    const int32_t jlo = self ? i + 1 : 0;
+    const int64_t e0 = it.ent_off, ne = it.n_act;
+    const int64_t rb_f = F.row_ptr[i];
+    const int64_t rb_b = SUBS ? B.row_ptr[i] : 0;
+    int64_t width = ((int64_t)n_cols - jlo + it.pieces - 1) / it.pieces;
+    int64_t out_n = 0;
+    unsigned long long n_rec = 0;
+    int64_t a = jlo;
+    int guard = 0;
+    while (a < n_cols) {
+        const int32_t z = (int32_t)(a + width < (int64_t)n_cols ? a + width : (int64_t)n_cols);
+        for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
+            s_key[x] = -1;
+            s_cnt[x] = 0;
+            s_s0[x] = SEED_NONE;
+            s_s1[x] = SEED_NONE;
+            if (SUBS) { s_cntb[x] = 0; s_b0[x] = SEED_NONE; s_b1[x] = SEED_NONE; }
         }
+        if (threadIdx.x == 0) { s_overflow = 0; s_nvalid = 0; }
+        __syncthreads();
+        // every cursor up to z
+        volatile int *ovf = &s_overflow;
+        for (int64_t e = e0 + threadIdx.x; e < e0 + ne; e += blockDim.x) {
+            if (*ovf) break;                     // the range is redone anyway
+            int32_t j = cur.nj[e];
+            if (j >= z) continue;
+            const uint32_t tt = cur.t[e];
+            const bool sb = SUBS && (tt & SIDE_B);
+            const int32_t *cs = sb ? B.col_seq : F.col_seq;
+            const uint16_t *cp = sb ? B.col_pos : F.col_pos;
+            uint32_t *cnt = sb ? s_cntb : s_cnt;
+            unsigned long long *q0 = sb ? s_b0 : s_s0, *q1 = sb ? s_b1 : s_s1;
+            const unsigned long long tv = (unsigned long long)(tt & ~SIDE_B) << 16;
+            int64_t x = cur.x[e];
+            const int64_t pe = cur.pe[e];
+            bool full = false;
+            for (;;) {
+                uint32_t slot = hash_j(j) & (uint32_t)(tsize - 1);
+                int probes = 0;
+                for (;;) {
+                    const int32_t prev = atomicCAS(&s_key[slot], -1, j);
+                    if (prev == -1 || prev == j) break;
+                    slot = (slot + 1) & (uint32_t)(tsize - 1);
+                    if (++probes >= tsize) { full = true; break; }
+                }
+                if (full) break;
+                atomicAdd(&cnt[slot], 1u);
+                const unsigned long long v = tv | (unsigned long long)cp[x];
+                const unsigned long long old = atomicMin(&q0[slot], v);
+                atomicMin(&q1[slot], old > v ? old : v);
+                if (++x >= pe) { j = J_DONE; break; }
+                j = cs[x];
+                if (j >= z) break;
+            }
+            if (full) { s_overflow = 1; continue; }
+            cur.x[e] = x;
+            cur.nj[e] = j;
+        }
+        __syncthreads();
+        if (s_overflow) {
+            // more distinct j in [a, z) than the table holds: every cursor back to a,
+            // and the range halved
+            for (int64_t e = e0 + threadIdx.x; e < e0 + ne; e += blockDim.x) {
+                const uint32_t tt = cur.t[e];
+                const bool sb = SUBS && (tt & SIDE_B);
+                const operand &L = sb ? B : F;
+                const int64_t t = (sb ? rb_b : rb_f) + (int64_t)(tt & ~SIDE_B);
+                const int64_t pb = L.col_ptr[L.row_code[t]], pe = cur.pe[e];
+                const int64_t x = lower_bound_seq(L.col_seq, pb, pe, (int32_t)a);
+                cur.x[e] = x;
+                cur.nj[e] = x < pe ? L.col_seq[x] : J_DONE;
+            }
+            __syncthreads();
+            if (z - a <= 1 || ++guard > 64) {          // cannot happen: one column fits any table
+                if (threadIdx.x == 0) { item_error[blockIdx.x] = 1; item_count[blockIdx.x] = 0; }
+                return;
+            }
+            width = (z - a) / 2;
+            continue;
+        }
+        // compact the passing entries of [a, z), sort them by j, append their records
+        for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
+            if (s_key[x] < 0) continue;
+            uint32_t c = s_cnt[x];
+            if (SUBS && s_cntb[x] > c) c = s_cntb[x];
+            if ((int64_t)c < (int64_t)min_shared) continue;
+            const int r = atomicAdd(&s_nvalid, 1);
+            s_sk[r] = (uint32_t)s_key[x];
+            s_sv[r] = (uint32_t)x;
+        }
+        __syncthreads();
+        const int nv = s_nvalid;
+        int np2 = 1;
+        while (np2 < nv) np2 <<= 1;
+        for (int x = nv + threadIdx.x; x < np2; x += blockDim.x) { s_sk[x] = 0xFFFFFFFFu; s_sv[x] = 0; }
+        __syncthreads();
+        bitonic_sort_pairs(s_sk, s_sv, np2);
+        if (out_n + nv > it.out_cap) {   // cannot happen: the capacity is the row's products
+            if (threadIdx.x == 0) { item_error[blockIdx.x] = 1; item_count[blockIdx.x] = 0; }
+            return;
+        }
+        for (int r = threadIdx.x; r < nv; r += blockDim.x) {
+            const int slot = (int)s_sv[r];
+            pastis_cand rec;
+            rec.i = i;
+            rec.j = (int32_t)s_sk[r];
+            const bool use_b = SUBS && (s_cntb[slot] > s_cnt[slot]);
+            unsigned long long sd[2];
+            int64_t rb;
+            const uint16_t *lpos;
+            if (use_b) {
+                rec.count = s_cntb[slot]; sd[0] = s_b0[slot]; sd[1] = s_b1[slot]; rb = rb_b; lpos = B.row_pos;
+            } else {
+                rec.count = s_cnt[slot]; sd[0] = s_s0[slot]; sd[1] = s_s1[slot]; rb = rb_f; lpos = F.row_pos;
+            }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            if (sd[q] == SEED_NONE) { rec.qpos[q] = 0xFFFF; rec.tpos[q] = 0xFFFF; continue; }
-            int64_t t = (int64_t)(sd[q] >> 16);
-            rec.qpos[q] = lpos[rb + t];
-            rec.tpos[q] = (uint16_t)(sd[q] & 0xFFFF);
+            for (int q = 0; q < 2; ++q) {
+                if (sd[q] == SEED_NONE) { rec.qpos[q] = 0xFFFF; rec.tpos[q] = 0xFFFF; continue; }
+                const int64_t t = (int64_t)(sd[q] >> 16);
+                rec.qpos[q] = lpos[rb + t];
+                rec.tpos[q] = (uint16_t)(sd[q] & 0xFFFF);
+            }
+            tmp_out[it.out_off + out_n + r] = rec;
         }
-        tmp_out[it.out_off + r] = rec;
+        out_n += nv;
+        n_rec += (unsigned long long)nv;
+        __syncthreads();                 // the table is cleared for the next range
+        a = z;
     }
-    if (threadIdx.x == 0) item_count[blockIdx.x] = nv;
-    if (stats) {                     // work of the items that completed (profiling only)
-        for (int x = 16; x > 0; x >>= 1) {
-            n_left += __shfl_xor_sync(0xffffffffu, n_left, x);
-            n_prod += __shfl_xor_sync(0xffffffffu, n_prod, x);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&stats[0], n_prod);
-            if (it.first) atomicAdd(&stats[1], n_left);   // each left entry once per row
-            if (threadIdx.x == 0) atomicAdd(&stats[2], (unsigned long long)nv);
-        }
+    if (threadIdx.x == 0) {
+        item_count[blockIdx.x] = out_n;
+        if (stats) atomicAdd(&stats[2], n_rec);
     }
 }
 
-__global__ void k_concat(const pastis_cand *tmp, const work_item *items, const int64_t *item_count,
-                         const int64_t *item_dst, int64_t n_items, pastis_cand *out) {
+__global__ void k_concat(const pastis_cand *tmp, const int64_t *src_off, const int64_t *dst_off, const int64_t *cnt,
+                         int64_t n_items, pastis_cand *out) {
     // one warp per item
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n_items) return;
-    const int64_t src = items[w].out_off, dst = item_dst[w], cnt = item_count[w];
-    for (int64_t r = lane; r < cnt; r += 32) out[dst + r] = tmp[src + r];
+    const int64_t src = src_off[w], dst = dst_off[w], c = cnt[w];
+    for (int64_t r = lane; r < c; r += 32) out[dst + r] = tmp[src + r];
 }
 
 size_t table_bytes(int tsize, bool subs) {
@@ -252,22 +336,22 @@ size_t table_bytes(int tsize, bool subs) {
 
 }  // namespace
 
-// The product driver.  Self mode (DB == nullptr): rows of A against A's postings,
-// columns j > i.  Query mode: rows of A (the queries) against the postings of DB,
-// every column j of DB (exact k-mers only).
 cudaError_t spgemm_set_smem_limit(size_t bytes) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_spgemm_items<true>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_spgemm_rows<true>);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spgemm_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_spgemm_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(bytes - fa.sharedSizeBytes));
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_spgemm_items<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_spgemm_rows<false>);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spgemm_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_spgemm_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(bytes - fa.sharedSizeBytes));
     return e;
 }
 
+// The product driver.  Self mode (DB == nullptr): rows of A against A's postings,
+// columns j > i.  Query mode: rows of A (the queries) against the postings of DB,
+// every column j of DB (exact k-mers only).
 static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const pastis_kmat *DB,
                                   const pastis_params *params, int32_t row_begin, int32_t row_end, pastis_cand *d_out,
                                   int64_t capacity, int64_t *n_out) {
@@ -321,213 +405,168 @@ static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const p
         Bop.col_ptr = AS.col_ptr; Bop.col_seq = AS.col_seq; Bop.col_pos = AS.col_pos;
     }
 
-    // per-row product bounds
-    int64_t *bound;
-    PASTIS_WS(bound, ctx, WS_SPG_ROWWORK, sizeof(int64_t) * 2 * (size_t)n);
-    int64_t *bound_b = bound + n;
-    prof_begin(ctx, "spgemm_bound");
-    k_row_bound<<<(unsigned)ceil_div64(n, 8), 256, 0, st>>>(F, n, bound);
+    // rows that can form products: left entries per row from the row pointers
+    const int32_t nr = row_end - row_begin;
+    std::vector<int64_t> rpf((size_t)nr + 1), rpb((size_t)nr + 1);
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(rpf.data(), F.row_ptr + row_begin, sizeof(int64_t) * (nr + 1),
+                                    cudaMemcpyDeviceToHost, st));
+    if (subs)
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(rpb.data(), Bop.row_ptr + row_begin, sizeof(int64_t) * (nr + 1),
+                                        cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int32_t> rows;
+    std::vector<int64_t> ent_off;
+    rows.reserve((size_t)nr);
+    ent_off.reserve((size_t)nr + 1);
+    int64_t n_ent = 0;
+    for (int32_t r = 0; r < nr; ++r) {
+        const int32_t i = row_begin + r;
+        if ((self ? i + 1 : 0) >= n_cols) continue;
+        const int64_t ne = (rpf[r + 1] - rpf[r]) + (subs ? rpb[r + 1] - rpb[r] : 0);
+        if (ne == 0) continue;
+        rows.push_back(i);
+        ent_off.push_back(n_ent);
+        n_ent += ne;
+    }
+    const int64_t ni = (int64_t)rows.size();
+    if (ni == 0) {
+        *n_out = 0;
+        return PASTIS_OK;
+    }
+
+    // cursors of every row (exact products per row)
+    cursors cur;
+    int32_t *d_rows;
+    PASTIS_WS(d_rows, ctx, WS_SPG_ROWWORK, (sizeof(int32_t) + 3 * sizeof(int64_t)) * (size_t)ni + 64);
+    int64_t *d_eoff = (int64_t *)(((uintptr_t)(d_rows + ni) + 7) & ~(uintptr_t)7);
+    int64_t *d_nact = d_eoff + ni;
+    int64_t *d_nprod = d_nact + ni;
+    char *cbuf;
+    PASTIS_WS(cbuf, ctx, WS_SPG_TABLE, (sizeof(int32_t) * 2 + sizeof(int64_t) * 2) * (size_t)n_ent + 64);
+    cur.x = (int64_t *)cbuf;
+    cur.pe = cur.x + n_ent;
+    cur.nj = (int32_t *)(cur.pe + n_ent);
+    cur.t = (uint32_t *)(cur.nj + n_ent);
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice, st));
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(d_eoff, ent_off.data(), sizeof(int64_t) * ni, cudaMemcpyHostToDevice, st));
+    unsigned long long *stats = ctx->prof_on ? ctx->d_stats : nullptr;
+    prof_begin(ctx, "spgemm_cursors");
+    k_spgemm_cursors<<<(unsigned)ceil_div64(ni * 32, CUR_THREADS), CUR_THREADS, 0, st>>>(
+        F, Bop, subs ? 1 : 0, self ? 1 : 0, d_rows, d_eoff, (int32_t)ni, cur, d_nact, d_nprod, stats);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
-    if (subs) {
-        prof_begin(ctx, "spgemm_bound");
-        k_row_bound<<<(unsigned)ceil_div64(n, 8), 256, 0, st>>>(Bop, n, bound_b);
-        PASTIS_LAUNCHED(ctx);
-        prof_end(ctx);
-    }
-    std::vector<int64_t> hb((size_t)n * (subs ? 2 : 1));
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(hb.data(), bound, sizeof(int64_t) * hb.size(), cudaMemcpyDeviceToHost, st));
+    std::vector<int64_t> nact((size_t)ni), nprod((size_t)ni);
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(nact.data(), d_nact, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(nprod.data(), d_nprod, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost, st));
     PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
 
-    // table size limit from shared memory
+    // plan: rows with products, each with a table size and a starting number of column
+    // ranges (distinct j <= products; ranges sized for a table half full)
     int tmax = 1 << 14;
     while (tmax > 64 && table_bytes(tmax, subs) + 64 > ctx->smem_optin) tmax >>= 1;
-
-    // plan: items by (i, column range), each with a table size
-    struct plan_item { int32_t i, j0, j1; int tlog; int64_t cap; };
-    std::vector<plan_item> plan;
-    plan.reserve((size_t)n);
-    for (int32_t i = row_begin; i < row_end; ++i) {
-        const int32_t jlo = self ? i + 1 : 0;
-        if (jlo >= n_cols) continue;
-        int64_t b = hb[i] + (subs ? hb[(size_t)n + i] : 0);
-        int64_t width = n_cols - jlo;
-        int64_t est = std::min(b, width);
-        if (est <= 0) continue;
+    int tl_max = 0;
+    while ((1 << tl_max) < tmax) ++tl_max;
+    struct plan_row { row_item it; int tlog; int64_t order; };
+    std::vector<plan_row> plan;
+    plan.reserve((size_t)ni);
+    int64_t tmp_total = 0;
+    for (int64_t r = 0; r < ni; ++r) {
+        if (nprod[r] == 0) continue;
+        const int32_t i = rows[r];
+        const int64_t width = (int64_t)n_cols - (self ? i + 1 : 0);
+        const int64_t est = std::min<int64_t>(nprod[r], width);
+        plan_row p;
+        p.it.i = i;
+        p.it.ent_off = ent_off[r];
+        p.it.n_act = nact[r];
+        p.it.out_cap = est;
+        p.order = r;
         if (est * 4 <= (int64_t)tmax * 3) {
             int tl = 6;
             while ((1ll << tl) * 3 < est * 4) ++tl;
-            plan.push_back({i, jlo, n_cols, tl, est});
+            p.tlog = tl;
+            p.it.pieces = 1;
         } else {
-            int tl = 0;
-            while ((1 << tl) < tmax) ++tl;
-            int64_t pieces = ceil_div64(est * 2, tmax);
-            for (int64_t q = 0; q < pieces; ++q) {
-                int32_t a = (int32_t)(jlo + (width * q) / pieces);
-                int32_t z = (int32_t)(jlo + (width * (q + 1)) / pieces);
-                if (z > a) plan.push_back({i, a, z, tl, std::min<int64_t>(std::min<int64_t>(b, z - a), tmax)});
-            }
+            p.tlog = tl_max;
+            p.it.pieces = (int32_t)std::min<int64_t>(width, ceil_div64(est * 2, tmax));
         }
+        p.it.out_off = tmp_total;
+        tmp_total += est;
+        plan.push_back(p);
     }
-
-    // upper bound of the records: distinct j per row
-    int64_t ubound = 0;
-    for (int32_t i = row_begin; i < row_end; ++i) {
-        const int32_t jlo = self ? i + 1 : 0;
-        if (jlo < n_cols) ubound += std::min<int64_t>(hb[i] + (subs ? hb[(size_t)n + i] : 0), (int64_t)(n_cols - jlo));
-    }
-    pastis_cand *result;
-    PASTIS_WS(result, ctx, WS_SPG_RESULT, sizeof(pastis_cand) * (size_t)(ubound + 1));
-
-    // run all pending items grouped by table size; split the ones that overflow and rerun
-    struct round_out { std::vector<plan_item> items; std::vector<int64_t> offs; std::vector<int64_t> cnts; };
-    std::vector<round_out> rounds_out;
-    int64_t tmp_total = 0;
-    int rounds = 0;
-    std::vector<plan_item> pending = plan;
-    while (!pending.empty()) {
-        if (++rounds > 24) return PASTIS_ERR_INTERNAL;
-        std::stable_sort(pending.begin(), pending.end(),
-                         [](const plan_item &a, const plan_item &b) { return a.tlog < b.tlog; });
-        const int64_t ni = (int64_t)pending.size();
-        std::vector<work_item> wi((size_t)ni);
-        int64_t off = 0;
-        for (int64_t x = 0; x < ni; ++x) {
-            wi[x].i = pending[x].i; wi[x].j0 = pending[x].j0; wi[x].j1 = pending[x].j1;
-            wi[x].first = pending[x].j0 == (self ? pending[x].i + 1 : 0);
-            wi[x].out_off = off; wi[x].out_cap = pending[x].cap;
-            off += pending[x].cap;
-        }
-        work_item *d_items;
-        PASTIS_WS(d_items, ctx, WS_SPG_BIN, sizeof(work_item) * ni + sizeof(int64_t) * 3 * ni + 64);
-        int64_t *d_cnt = (int64_t *)(d_items + ni);
-        int *d_ovf = (int *)(d_cnt + ni);
+    const int64_t np = (int64_t)plan.size();
+    int64_t total = 0;
+    pastis_cand *result = nullptr;
+    if (np > 0) {
+        std::stable_sort(plan.begin(), plan.end(), [](const plan_row &a, const plan_row &b) { return a.tlog < b.tlog; });
+        std::vector<row_item> wi((size_t)np);
+        for (int64_t x = 0; x < np; ++x) wi[x] = plan[x].it;
+        row_item *d_items;
+        PASTIS_WS(d_items, ctx, WS_SPG_BIN, sizeof(row_item) * np + (sizeof(int64_t) + sizeof(int)) * np + 64);
+        int64_t *d_cnt = (int64_t *)(d_items + np);
+        int *d_err = (int *)(d_cnt + np);
         pastis_cand *tmp;
-        PASTIS_WS(tmp, ctx, WS_SPG_TMP, sizeof(pastis_cand) * (size_t)(off + 1));
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(d_items, wi.data(), sizeof(work_item) * ni, cudaMemcpyHostToDevice, st));
-        PASTIS_CUDA_TRY(cudaMemsetAsync(d_ovf, 0, sizeof(int) * ni, st));
+        PASTIS_WS(tmp, ctx, WS_SPG_TMP, sizeof(pastis_cand) * (size_t)(tmp_total + 1));
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(d_items, wi.data(), sizeof(row_item) * np, cudaMemcpyHostToDevice, st));
+        PASTIS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int) * np, st));
         int64_t x0 = 0;
-        while (x0 < ni) {
+        while (x0 < np) {
             int64_t x1 = x0;
-            while (x1 < ni && pending[x1].tlog == pending[x0].tlog) ++x1;
-            const int tsize = 1 << pending[x0].tlog;
+            while (x1 < np && plan[x1].tlog == plan[x0].tlog) ++x1;
+            const int tsize = 1 << plan[x0].tlog;
             const size_t shm = table_bytes(tsize, subs);
             for (int64_t g0 = x0; g0 < x1; g0 += 65535) {
-                int64_t g1 = std::min<int64_t>(x1, g0 + 65535);
-                prof_begin(ctx, "spgemm_items");
+                const int64_t g1 = std::min<int64_t>(x1, g0 + 65535);
+                prof_begin(ctx, "spgemm_rows");
                 if (subs)
-                    k_spgemm_items<true><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
-                        F, Bop, d_items + g0, tsize, params->min_shared, tmp, d_cnt + g0, d_ovf + g0,
-                        ctx->prof_on ? ctx->d_stats : nullptr);
+                    k_spgemm_rows<true><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
+                        F, Bop, d_items + g0, tsize, params->min_shared, self ? 1 : 0, n_cols, cur, tmp, d_cnt + g0,
+                        d_err + g0, stats);
                 else
-                    k_spgemm_items<false><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
-                        F, Bop, d_items + g0, tsize, params->min_shared, tmp, d_cnt + g0, d_ovf + g0,
-                        ctx->prof_on ? ctx->d_stats : nullptr);
+                    k_spgemm_rows<false><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
+                        F, Bop, d_items + g0, tsize, params->min_shared, self ? 1 : 0, n_cols, cur, tmp, d_cnt + g0,
+                        d_err + g0, stats);
                 PASTIS_LAUNCHED(ctx);
                 prof_end(ctx);
             }
             x0 = x1;
         }
-        std::vector<int64_t> hc((size_t)ni);
-        std::vector<int> ho((size_t)ni);
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(hc.data(), d_cnt, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost, st));
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(ho.data(), d_ovf, sizeof(int) * ni, cudaMemcpyDeviceToHost, st));
+        std::vector<int64_t> hc((size_t)np);
+        std::vector<int> he((size_t)np);
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(hc.data(), d_cnt, sizeof(int64_t) * np, cudaMemcpyDeviceToHost, st));
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(he.data(), d_err, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
         PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
-        round_out ro;
-        std::vector<plan_item> next;
-        int tl_max = 0;
-        while ((1 << tl_max) < tmax) ++tl_max;
-        for (int64_t x = 0; x < ni; ++x) {
-            if (ho[x]) {
-                // grow the table to the maximum first, then halve the column range
-                plan_item p = pending[x];
-                if (p.tlog < tl_max) {
-                    p.tlog = tl_max;
-                    p.cap = std::min<int64_t>((int64_t)p.j1 - p.j0, (int64_t)tmax);
-                    next.push_back(p);
-                    continue;
-                }
-                if (p.j1 - p.j0 < 2) return PASTIS_ERR_INTERNAL;
-                int32_t mid = p.j0 + (p.j1 - p.j0) / 2;
-                next.push_back({p.i, p.j0, mid, p.tlog, std::min<int64_t>((int64_t)tmax, mid - p.j0)});
-                next.push_back({p.i, mid, p.j1, p.tlog, std::min<int64_t>((int64_t)tmax, p.j1 - mid)});
-                continue;
-            }
-            if (hc[x] > 0) {
-                ro.items.push_back(pending[x]);
-                ro.offs.push_back(wi[x].out_off);
-                ro.cnts.push_back(hc[x]);
-            }
+        // slices in row order
+        std::vector<int64_t> ord((size_t)np);
+        for (int64_t x = 0; x < np; ++x) {
+            if (he[x]) return PASTIS_ERR_INTERNAL;
+            ord[x] = x;
         }
-        // gather this round's slices, in (i, j0) order, into the result area after the
-        // earlier rounds
-        const int64_t nk = (int64_t)ro.items.size();
+        std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return plan[a].order < plan[b].order; });
+        std::vector<int64_t> src, dst, cnt;
+        for (int64_t x : ord) {
+            if (hc[x] == 0) continue;
+            src.push_back(plan[x].it.out_off);
+            dst.push_back(total);
+            cnt.push_back(hc[x]);
+            total += hc[x];
+        }
+        PASTIS_WS(result, ctx, WS_SPG_RESULT, sizeof(pastis_cand) * (size_t)(total + 1));
+        const int64_t nk = (int64_t)src.size();
         if (nk > 0) {
-            std::vector<int64_t> ord((size_t)nk);
-            for (int64_t x = 0; x < nk; ++x) ord[x] = x;
-            std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
-                return ro.items[a].i != ro.items[b].i ? ro.items[a].i < ro.items[b].i : ro.items[a].j0 < ro.items[b].j0;
-            });
-            round_out sorted;
-            for (int64_t x : ord) {
-                sorted.items.push_back(ro.items[x]);
-                sorted.offs.push_back(ro.offs[x]);
-                sorted.cnts.push_back(ro.cnts[x]);
-            }
-            ro = sorted;
-            std::vector<work_item> src((size_t)nk);
-            std::vector<int64_t> dst((size_t)nk);
-            for (int64_t x = 0; x < nk; ++x) {
-                src[x].out_off = ro.offs[x];
-                dst[x] = tmp_total;
-                ro.offs[x] = tmp_total;   // now the position in the result area
-                tmp_total += ro.cnts[x];
-            }
-            if (tmp_total > ubound) return PASTIS_ERR_INTERNAL;
-            work_item *d_src;
-            PASTIS_WS(d_src, ctx, WS_SPG_ROWOFF, (sizeof(work_item) + 2 * sizeof(int64_t)) * (size_t)nk + 64);
-            int64_t *d_dst = (int64_t *)(d_src + nk);
+            int64_t *d_src;
+            PASTIS_WS(d_src, ctx, WS_SPG_ROWOFF, 3 * sizeof(int64_t) * (size_t)nk + 64);
+            int64_t *d_dst = d_src + nk;
             int64_t *d_c = d_dst + nk;
-            PASTIS_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), sizeof(work_item) * nk, cudaMemcpyHostToDevice, st));
+            PASTIS_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), sizeof(int64_t) * nk, cudaMemcpyHostToDevice, st));
             PASTIS_CUDA_TRY(cudaMemcpyAsync(d_dst, dst.data(), sizeof(int64_t) * nk, cudaMemcpyHostToDevice, st));
-            PASTIS_CUDA_TRY(cudaMemcpyAsync(d_c, ro.cnts.data(), sizeof(int64_t) * nk, cudaMemcpyHostToDevice, st));
+            PASTIS_CUDA_TRY(cudaMemcpyAsync(d_c, cnt.data(), sizeof(int64_t) * nk, cudaMemcpyHostToDevice, st));
             prof_begin(ctx, "spgemm_concat");
-            k_concat<<<(unsigned)ceil_div64(nk * 32, 256), 256, 0, st>>>(tmp, d_src, d_c, d_dst, nk, result);
+            k_concat<<<(unsigned)ceil_div64(nk * 32, 256), 256, 0, st>>>(tmp, d_src, d_dst, d_c, nk, result);
             PASTIS_LAUNCHED(ctx);
             prof_end(ctx);
             PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
         }
-        rounds_out.push_back(ro);
-        pending.swap(next);
-    }
-    // final order: all kept slices sorted by (i, j0); a single round is already in order
-    int64_t total = tmp_total;
-    if (rounds_out.size() > 1 && total > 0) {
-        struct sl { int32_t i, j0; int64_t off, cnt; };
-        std::vector<sl> all;
-        for (auto &ro : rounds_out)
-            for (size_t x = 0; x < ro.items.size(); ++x) all.push_back({ro.items[x].i, ro.items[x].j0, ro.offs[x], ro.cnts[x]});
-        std::sort(all.begin(), all.end(), [](const sl &a, const sl &b) { return a.i != b.i ? a.i < b.i : a.j0 < b.j0; });
-        const int64_t nk = (int64_t)all.size();
-        std::vector<work_item> src((size_t)nk);
-        std::vector<int64_t> dst((size_t)nk), cnt((size_t)nk);
-        int64_t acc = 0;
-        for (int64_t x = 0; x < nk; ++x) { src[x].out_off = all[x].off; dst[x] = acc; cnt[x] = all[x].cnt; acc += cnt[x]; }
-        pastis_cand *tmp2;
-        PASTIS_WS(tmp2, ctx, WS_SPG_TMP, sizeof(pastis_cand) * (size_t)(total + 1));
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(tmp2, result, sizeof(pastis_cand) * total, cudaMemcpyDeviceToDevice, st));
-        work_item *d_src;
-        PASTIS_WS(d_src, ctx, WS_SPG_ROWOFF, (sizeof(work_item) + 2 * sizeof(int64_t)) * (size_t)nk + 64);
-        int64_t *d_dst = (int64_t *)(d_src + nk);
-        int64_t *d_c = d_dst + nk;
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), sizeof(work_item) * nk, cudaMemcpyHostToDevice, st));
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(d_dst, dst.data(), sizeof(int64_t) * nk, cudaMemcpyHostToDevice, st));
-        PASTIS_CUDA_TRY(cudaMemcpyAsync(d_c, cnt.data(), sizeof(int64_t) * nk, cudaMemcpyHostToDevice, st));
-        prof_begin(ctx, "spgemm_concat");
-        k_concat<<<(unsigned)ceil_div64(nk * 32, 256), 256, 0, st>>>(tmp2, d_src, d_c, d_dst, nk, result);
-        PASTIS_LAUNCHED(ctx);
-        prof_end(ctx);
-        PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
     }
     ctx->spg_valid = 1;
     ctx->spg_n = total;

@@ -131,9 +131,30 @@ def test_candidates_exact_edge_cases(P, ctx):
 
 
 def test_candidates_split_rows(P, ctx):
-    # many copies of one family: rows exceed a shared-memory table and are split
+    # many copies of one family: rows with many partners, tables up to their limit
     fam = synth.planted_families([700], 0, (60, 120), seed=11)
     got, want = _cands(P, ctx, fam, k=3)
+    assert got.tobytes() == want.tobytes()
+
+
+def _shared_kmer_set():
+    # 4,400 sequences holding one common 6-mer (WWWWWW, W nowhere else) among 20,000
+    # unrelated ones: the first rows have more distinct partners than a table holds,
+    # all of them in the first column range the product bound suggests, so the row
+    # takes several ranges and the first ones overflow and are halved
+    rng = np.random.default_rng(1)
+    alpha = np.frombuffer(b"ARNDCQEGHILKMFPSTYV", dtype=np.uint8)
+    rnd = lambda n: rng.choice(alpha, n).tobytes().decode()
+    strs = ["WWWWWW" + rnd(20)] + [rnd(10) + "WWWWWW" + rnd(10) for _ in range(4400)]
+    strs += [rnd(30) for _ in range(20000)]
+    return synth.from_strings(strs)
+
+
+@pytest.mark.parametrize("m", [0, 3])
+def test_candidates_rows_in_column_ranges(P, ctx, m):
+    got, want = _cands(P, ctx, _shared_kmer_set(), k=6, m=m)
+    assert len(want) > 9_000_000
+    assert len(got) == len(want)
     assert got.tobytes() == want.tobytes()
 
 
@@ -287,7 +308,7 @@ def test_profiler_counts_kernels(P, ctx):
         prof = ctx.profile_read()
         st = ctx.stats()
         ctx.profile(False)
-        for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_items", "sw_pass1", "sw_pass3",
+        for name in ("encode", "kmer_windows", "radix_scatter", "spgemm_cursors", "spgemm_rows", "sw_pass1", "sw_pass3",
                      "filter_flags"):
             assert name in prof and prof[name][0] >= 1 and prof[name][1] >= 0.0, name
         if it == 0:
