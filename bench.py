@@ -526,13 +526,38 @@ def run_serve(args):
     for q in reqs[:3]:
         srv.submit(q.ascii, q.offsets).future.result()
     ctx = P.Context(0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n_edges_batch = 0
-    for q in reqs:
-        n_edges_batch += len(srv.process(ctx, S.Request(q.ascii, q.offsets, 0)))
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+
+    def batch_path():
+        """Every request in turn on one context; per-request times and edges."""
+        times, n_e = [], 0
+        torch.cuda.synchronize()
+        t_all = time.perf_counter()
+        for q in reqs:
+            t1 = time.perf_counter()
+            n_e += len(srv.process(ctx, S.Request(q.ascii, q.offsets, 0)))
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+        return time.perf_counter() - t_all, n_e, np.array(times)
+
+    graphs = None
+    if args.no_graphs:
+        srv.graphs = False
+    else:
+        # the same requests with the direct alignment call, for the graphs' effect
+        srv.graphs = False
+        batch_path()
+        t_direct, _, times_direct = batch_path()
+        srv.graphs = True
+        batch_path()
+    t_batch, n_edges_batch, times = batch_path()
+    if not args.no_graphs:
+        small = sizes <= 16
+        graphs = {"alignment": "captured CUDA graph per worker context (pastis_align_plan)",
+                  "batch_path_s_graphs": round(t_batch, 3), "batch_path_s_direct": round(t_direct, 3),
+                  "median_request_ms_le16_queries_graphs": round(1e3 * float(np.median(times[small])), 3),
+                  "median_request_ms_le16_queries_direct": round(1e3 * float(np.median(times_direct[small])), 3),
+                  "requests_le16_queries": int(small.sum())}
+    srv.drop_plan(ctx)
     ctx.close()
     nq = int(sizes.sum())
     cap = nq / t_batch
@@ -562,6 +587,7 @@ def run_serve(args):
             srv.process(ctx, S.Request(q.ascii, q.offsets, 0))
         torch.cuda.synchronize()
         cap_pf = nq / (time.perf_counter() - t0)
+        srv.drop_plan(ctx)
         ctx.close()
         srv.done.clear()
         handles = []
@@ -590,7 +616,7 @@ def run_serve(args):
                        "slots": args.slots},
             "p50_s": st["p50_s"], "p99_s": st["p99_s"], "queries": nq,
             "batch_path_queries_per_s": cap, "edges": n_edges, "edges_batch_path": n_edges_batch,
-            "prefiltered": pf}
+            "graphs": graphs, "prefiltered": pf}
     print(json.dumps(line), flush=True)
     return 0 if n_edges == n_edges_batch else 1
 
@@ -619,6 +645,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="serve mode: concurrent worker slots")
     ap.add_argument("--prefilter", action="store_true",
                     help="serve mode: also run the stream through the learned prefilter")
+    ap.add_argument("--no-graphs", action="store_true", help="serve mode: direct alignment calls, no CUDA graphs")
     ap.add_argument("--recall", type=float, default=0.995, help="edge recall the prefilter must keep")
     ap.add_argument("--calib-recall", type=float, default=0.998,
                     help="recall the threshold is calibrated for on the calibration block (margin over --recall)")

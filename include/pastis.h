@@ -286,6 +286,44 @@ pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const
                                  const pastis_params *params, int32_t reps, uint8_t *h_extra,
                                  int64_t *h_cycles);
 
+/* ---- batching: alignment plans replayed as CUDA graphs ------------------------------
+ * A plan captures the whole alignment of one batch (the input checks, then pass 1-3 of
+ * PASTIS_SW / PASTIS_SW_SCORE or the x-drop extensions and their combination) once, as
+ * a CUDA graph over buffers of fixed capacity, against a target set that stays resident
+ * (the serving form: the database).  Each run copies the batch into the plan's buffers,
+ * writes its counts to device memory and launches the graph: one launch and one
+ * synchronisation instead of a launch per kernel and a synchronisation per stage.  The
+ * kernels are the ones pastis_align_pairs_qt runs, sized for the capacity (persistent
+ * grids, scans over the capacity with zero counts past the batch), so every record
+ * equals pastis_align_pairs_qt's on the same batch.
+ *
+ * pastis_align_plan_create: ctx supplies the device, the stream (the plan runs on it)
+ *   and the pass-1 layout at this moment; the plan owns a private workspace.  Targets
+ *   d_tcodes / d_toffsets[n_t+1] (device; they must stay valid and unchanged while the
+ *   plan lives) are checked once: a code >= 24 gives PASTIS_ERR_INVALID_RESIDUE, a
+ *   target longer than max_len PASTIS_ERR_INVALID_ARG.  Capacities: max_q queries,
+ *   max_qres query residues, max_pairs pairs, max_len residues per query or target
+ *   (<= 65535).  params is copied (every mode).  Synchronises.
+ * pastis_align_plan_run: queries d_qcodes (device) with offsets h_qoffsets[n_q+1] on the
+ *   HOST (h_qoffsets[0] = 0, non-decreasing, else PASTIS_ERR_INVALID_ARG), pairs
+ *   d_pairs[n_pairs] (device) as for pastis_align_pairs_qt, records to d_out[n_pairs]
+ *   (device).  A batch above a capacity (n_q, n_pairs, residues, a query longer than
+ *   max_len) gives PASTIS_ERR_CAPACITY before any work; a pair naming a sequence
+ *   outside the batch or the targets (or an x-drop seed that does not fit) gives
+ *   PASTIS_ERR_INVALID_ARG, a query code >= 24 PASTIS_ERR_INVALID_RESIDUE; then the
+ *   alignment kernels have done nothing, d_out is untouched and the plan stays usable.
+ *   Synchronises.
+ * pastis_align_plan_destroy: waits for the plan's stream and frees everything.
+ * pastis_align_plan_graph_nodes: nodes of the captured graph (-1 on error).         */
+typedef struct pastis_align_plan pastis_align_plan;
+pastis_status pastis_align_plan_create(pastis_ctx *ctx, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                       int32_t n_t, int32_t max_q, int64_t max_qres, int64_t max_pairs,
+                                       int32_t max_len, const pastis_params *params, pastis_align_plan **out);
+pastis_status pastis_align_plan_run(pastis_align_plan *plan, const uint8_t *d_qcodes, const int64_t *h_qoffsets,
+                                    int32_t n_q, const pastis_cand *d_pairs, int64_t n_pairs, pastis_aln *d_out);
+pastis_status pastis_align_plan_destroy(pastis_align_plan *plan);
+int64_t pastis_align_plan_graph_nodes(const pastis_align_plan *plan);
+
 /* ---- a10: similarity filter (Sec. IV-F, VI-B) ----------------------------------- */
 
 /* Keeps pair p iff cols > 0, 100*ident >= ani*cols and 100*span >= cov*len, span and

@@ -5,6 +5,6 @@ x-drop alignment -> ANI/coverage similarity filter, all in hand-written CUDA beh
 C ABI of include/pastis.h.  `pastis` is the thin Python binding of that library.
 """
 from . import pastis
-from .pastis import (ALN_DTYPE, CAND_DTYPE, EDGE_DTYPE, SW, XD, Context, KMat, Params, PastisError,
+from .pastis import (ALN_DTYPE, CAND_DTYPE, EDGE_DTYPE, SW, XD, AlignPlan, Context, KMat, Params, PastisError,
                      align_pairs, autotune_sw, build_kmers, encode, filter_edges, overlap_spgemm, run,
                      substitute_kmers, to_records)

@@ -9,6 +9,7 @@
 // (identities << 16 | matched columns) along the predecessor a traceback would take
 // (diagonal > F > E, open > extend), so the end cell holds the path's statistics.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -16,7 +17,8 @@
 
 pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, const uint8_t *d_tcodes,
                        const int64_t *d_toffsets, const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *p,
-                       const int8_t *dmat, int *flags, int lmax, pastis_aln *d_out, int64_t *d_cells);
+                       const int8_t *dmat, int *flags, int lmax, pastis_aln *d_out, int64_t *d_cells,
+                       const int64_t *dn, const int *chk);
 
 namespace {
 
@@ -280,7 +282,10 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, c
                                                         const uint8_t *tcodes, const int64_t *toffsets,
                                                         const pastis_cand *pairs, int64_t n_pairs, int k,
                                                         const int8_t *gmat, int o, int e, int X, int32_t *gbuf,
-                                                        int W, int *next_task, ext_out *out) {
+                                                        int W, int *next_task, ext_out *out, const int64_t *dn,
+                                                        const int *chk) {
+    if (dn) n_pairs = *dn;                       // captured launches: count in device memory
+    if (chk && (chk[0] | chk[1])) return;        // ... and nothing on bad input
     __shared__ int s_mat[(PASTIS_NSYM + 1) * 32];
     load_matrix(gmat, s_mat);
     __syncthreads();
@@ -320,7 +325,9 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, c
 __global__ void k_xd_combine(const uint8_t *qcodes, const int64_t *qoffsets, const uint8_t *tcodes,
                              const int64_t *toffsets, const pastis_cand *pairs,
                              int64_t n_pairs, int k, const int8_t *gmat, int ani, int cov, const ext_out *ext,
-                             pastis_aln *out, unsigned long long *cells) {
+                             pastis_aln *out, unsigned long long *cells, const int64_t *dn, const int *chk) {
+    if (dn) n_pairs = *dn;
+    if (chk && (chk[0] | chk[1])) return;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long my = 0;
     if (p < n_pairs) {
@@ -375,13 +382,15 @@ __global__ void k_max_len(const int64_t *offsets, int32_t n, int *mx) {
     if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
 }
 
-__global__ void k_check_codes(const uint8_t *codes, int64_t n, int *bad) {
+__global__ void k_check_codes(const uint8_t *codes, int64_t n, int *bad, const int64_t *dn) {
+    if (dn) n = *dn;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         if (codes[x] >= PASTIS_NSYM) *bad = 1;
 }
 
 __global__ void k_check_pairs(const pastis_cand *pairs, int64_t n_pairs, const int64_t *qoffsets, int32_t n_q,
-                              const int64_t *toffsets, int32_t n_t, int k, int xd, int *bad) {
+                              const int64_t *toffsets, int32_t n_t, int k, int xd, int *bad, const int64_t *dc) {
+    if (dc) { n_pairs = dc[0]; n_q = (int32_t)dc[2]; }
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
     const pastis_cand c = pairs[p];
@@ -395,10 +404,18 @@ __global__ void k_check_pairs(const pastis_cand *pairs, int64_t n_pairs, const i
 
 }  // namespace
 
+// A captured launch sequence (the plan's graph): counts in device memory, sizes at
+// the plan's capacities, no host synchronisation inside.
+struct align_graph {
+    const int64_t *dc;     // [0] pairs, [1] query residues, [2] queries
+    int lmax;              // the longest sequence the plan admits
+    int64_t qres_cap;      // capacity of the query residues
+};
+
 static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, int32_t n_q,
                               const uint8_t *d_tcodes, const int64_t *d_toffsets, int32_t n_t,
                               const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *params,
-                              pastis_aln *d_out, int64_t *d_cells) {
+                              pastis_aln *d_out, int64_t *d_cells, const align_graph *g = nullptr) {
     if (!ctx || n_pairs < 0 || n_q < 0 || n_t < 0) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
@@ -415,36 +432,52 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     memcpy(hconst, params->matrix, 576);
     memset(hconst + 576, 0, 64);
     memcpy(hconst + 640, ctx->sw_lay.extra, PASTIS_SW_BINS);
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, hconst, sizeof(hconst), cudaMemcpyHostToDevice, st));
+    if (!g) PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, hconst, sizeof(hconst), cudaMemcpyHostToDevice, st));
     PASTIS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64, st));
     const int xd = params->mode == PASTIS_XD;
-    k_max_len<<<(unsigned)ceil_div64(n_q, 256), 256, 0, st>>>(d_qoffsets, n_q, flags + 2);
-    PASTIS_LAUNCHED(ctx);
-    k_max_len<<<(unsigned)ceil_div64(n_t, 256), 256, 0, st>>>(d_toffsets, n_t, flags + 2);
-    PASTIS_LAUNCHED(ctx);
-    k_check_pairs<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, n_q, d_toffsets,
-                                                                     n_t, params->k, xd, flags + 4);
-    PASTIS_LAUNCHED(ctx);
-    int64_t h_end[2] = {0, 0};
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_end[0], d_qoffsets + n_q, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_end[1], d_toffsets + n_t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int w = 0; w < 2; ++w) {
-        const uint8_t *cd = w == 0 ? d_qcodes : d_tcodes;
-        if (h_end[w] > 0 && (w == 0 || cd != d_qcodes)) {
-            int blocks_c = (int)std::min<int64_t>(ceil_div64(h_end[w], 256), (int64_t)ctx->sm_count * 16);
-            prof_begin(ctx, "align_checks");
-            k_check_codes<<<blocks_c, 256, 0, st>>>(cd, h_end[w], flags + 5);
-            PASTIS_LAUNCHED(ctx);
-            prof_end(ctx);
-        }
+    const int64_t *dn = g ? g->dc : nullptr;
+    const int *chk = g ? flags + 4 : nullptr;
+    if (g) {
+        // the plan checked the lengths on the host; the pairs and the query residues here
+        k_check_pairs<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, n_q,
+                                                                         d_toffsets, n_t, params->k, xd, flags + 4,
+                                                                         g->dc);
+        PASTIS_LAUNCHED(ctx);
+        const int blocks_c = (int)std::min<int64_t>(ceil_div64(g->qres_cap, 256), (int64_t)ctx->sm_count * 16);
+        k_check_codes<<<blocks_c, 256, 0, st>>>(d_qcodes, g->qres_cap, flags + 5, g->dc + 1);
+        PASTIS_LAUNCHED(ctx);
     }
-    int hf[6];
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
-    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hf[4]) return PASTIS_ERR_INVALID_ARG;
-    if (hf[5]) return PASTIS_ERR_INVALID_RESIDUE;
-    const int lmax = hf[2];
+    int lmax = g ? g->lmax : 0;
+    if (!g) {
+        k_max_len<<<(unsigned)ceil_div64(n_q, 256), 256, 0, st>>>(d_qoffsets, n_q, flags + 2);
+        PASTIS_LAUNCHED(ctx);
+        k_max_len<<<(unsigned)ceil_div64(n_t, 256), 256, 0, st>>>(d_toffsets, n_t, flags + 2);
+        PASTIS_LAUNCHED(ctx);
+        k_check_pairs<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, n_q,
+                                                                         d_toffsets, n_t, params->k, xd, flags + 4,
+                                                                         nullptr);
+        PASTIS_LAUNCHED(ctx);
+        int64_t h_end[2] = {0, 0};
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_end[0], d_qoffsets + n_q, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_end[1], d_toffsets + n_t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int w = 0; w < 2; ++w) {
+            const uint8_t *cd = w == 0 ? d_qcodes : d_tcodes;
+            if (h_end[w] > 0 && (w == 0 || cd != d_qcodes)) {
+                int blocks_c = (int)std::min<int64_t>(ceil_div64(h_end[w], 256), (int64_t)ctx->sm_count * 16);
+                prof_begin(ctx, "align_checks");
+                k_check_codes<<<blocks_c, 256, 0, st>>>(cd, h_end[w], flags + 5, nullptr);
+                PASTIS_LAUNCHED(ctx);
+                prof_end(ctx);
+            }
+        }
+        int hf[6];
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+        PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hf[4]) return PASTIS_ERR_INVALID_ARG;
+        if (hf[5]) return PASTIS_ERR_INVALID_RESIDUE;
+        lmax = hf[2];
+    }
     if (lmax > PASTIS_MAX_LEN) return PASTIS_ERR_INVALID_ARG;
     int xd_per_sm = 2;
     if (xd) {
@@ -455,7 +488,7 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     const int nwarps = blocks * ALN_WARPS;
     if (!xd) {
         s = sw_align(ctx, d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params, dmat, flags, lmax,
-                     d_out, d_cells);
+                     d_out, d_cells, dn, chk);
         if (s != PASTIS_OK) return s;
     } else {
         const int W = lmax + 2;
@@ -466,16 +499,17 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
         prof_begin(ctx, "xd_extend");
         k_xd_ext<<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs,
                                                  params->k, dmat, params->gap_open, params->gap_extend, params->xdrop,
-                                                 gbuf, W, flags + 6, ext);
+                                                 gbuf, W, flags + 6, ext, dn, chk);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
         prof_begin(ctx, "xd_combine");
         k_xd_combine<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(
             d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat, params->ani_min_pct,
-            params->cov_min_pct, ext, d_out, (unsigned long long *)d_cells);
+            params->cov_min_pct, ext, d_out, (unsigned long long *)d_cells, dn, chk);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
     }
+    if (g) return PASTIS_OK;                 // the plan reads the flags after its launch
     int herr = 0;
     PASTIS_CUDA_TRY(cudaMemcpyAsync(&herr, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -568,4 +602,196 @@ extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qc
     if (h_cycles)
         for (int x = 0; x < NX * PASTIS_SW_BINS; ++x) h_cycles[x] = cyc[x];
     return PASTIS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Alignment plans: the whole alignment of one batch captured once as a CUDA graph over
+// fixed-capacity buffers, replayed per batch with the counts in device memory.
+// ---------------------------------------------------------------------------------
+struct pastis_align_plan {
+    pastis_ctx *ctx;                 // private workspace on the plan's own stream
+    cudaStream_t stream;             // non-blocking: capture is not possible on a default stream
+    cudaStream_t caller;             // the stream of the context the plan was made from
+    cudaEvent_t ready;               // orders each run after the caller's earlier work
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    uint8_t *qcodes;
+    int64_t *qoffsets;
+    pastis_cand *pairs;
+    pastis_aln *out;
+    int64_t *dc;                     // [0] pairs, [1] query residues, [2] queries
+    int64_t *h_dc;                   // pinned staging of dc
+    const uint8_t *tcodes;
+    const int64_t *toffsets;
+    int32_t n_t, max_q, max_len;
+    int64_t max_qres, max_pairs;
+    pastis_params params;
+};
+
+static void plan_free(pastis_align_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->qcodes) cudaFree(p->qcodes);
+    if (p->qoffsets) cudaFree(p->qoffsets);
+    if (p->pairs) cudaFree(p->pairs);
+    if (p->out) cudaFree(p->out);
+    if (p->dc) cudaFree(p->dc);
+    if (p->h_dc) cudaFreeHost(p->h_dc);
+    if (p->ctx) pastis_ctx_destroy(p->ctx);
+    if (p->ready) cudaEventDestroy(p->ready);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    free(p);
+}
+
+extern "C" pastis_status pastis_align_plan_create(pastis_ctx *ctx, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                                  int32_t n_t, int32_t max_q, int64_t max_qres, int64_t max_pairs,
+                                                  int32_t max_len, const pastis_params *params,
+                                                  pastis_align_plan **out) {
+    if (!out) return PASTIS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctx || !d_tcodes || !d_toffsets || n_t < 1 || max_q < 1 || max_qres < 1 || max_pairs < 1 || max_len < 1 ||
+        max_len > PASTIS_MAX_LEN || max_q > INT32_MAX - 1)
+        return PASTIS_ERR_INVALID_ARG;
+    pastis_status s = check_params(params);
+    if (s != PASTIS_OK) return s;
+    cudaStream_t st = ctx->stream;
+    // the targets once: lengths within max_len, codes valid
+    int *tf;
+    PASTIS_WS(tf, ctx, WS_FLAGS, 1024);
+    int *fl = (int *)((int8_t *)tf + 768);
+    PASTIS_CUDA_TRY(cudaMemsetAsync(fl, 0, 64, st));
+    k_max_len<<<(unsigned)ceil_div64(n_t, 256), 256, 0, st>>>(d_toffsets, n_t, fl + 2);
+    PASTIS_LAUNCHED(ctx);
+    int64_t t_end = 0;
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(&t_end, d_toffsets + n_t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (t_end > 0) {
+        const int blocks_c = (int)std::min<int64_t>(ceil_div64(t_end, 256), (int64_t)ctx->sm_count * 16);
+        k_check_codes<<<blocks_c, 256, 0, st>>>(d_tcodes, t_end, fl + 5, nullptr);
+        PASTIS_LAUNCHED(ctx);
+    }
+    int hf[6];
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(hf, fl, sizeof(hf), cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hf[5]) return PASTIS_ERR_INVALID_RESIDUE;
+    if (hf[2] > max_len) return PASTIS_ERR_INVALID_ARG;
+
+    pastis_align_plan *p = (pastis_align_plan *)calloc(1, sizeof(pastis_align_plan));
+    if (!p) return PASTIS_ERR_OUT_OF_MEMORY;
+    p->tcodes = d_tcodes; p->toffsets = d_toffsets; p->n_t = n_t;
+    p->max_q = max_q; p->max_qres = max_qres; p->max_pairs = max_pairs; p->max_len = max_len;
+    p->params = *params;
+    p->caller = st;
+    if (cudaSetDevice(ctx->device) != cudaSuccess || cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(p);
+        return PASTIS_ERR_CUDA;
+    }
+    st = p->stream;
+    s = pastis_ctx_create(&p->ctx, ctx->device, (void *)st);
+    if (s != PASTIS_OK) { plan_free(p); return s; }
+    p->ctx->sw_lay = ctx->sw_lay;
+#define PLAN_TRY(expr) do { if ((expr) != cudaSuccess) { cudaGetLastError(); plan_free(p); return PASTIS_ERR_OUT_OF_MEMORY; } } while (0)
+    PLAN_TRY(cudaMalloc(&p->qcodes, (size_t)max_qres + 16));
+    PLAN_TRY(cudaMalloc(&p->qoffsets, sizeof(int64_t) * ((size_t)max_q + 1)));
+    PLAN_TRY(cudaMalloc(&p->pairs, sizeof(pastis_cand) * (size_t)max_pairs));
+    PLAN_TRY(cudaMalloc(&p->out, sizeof(pastis_aln) * (size_t)max_pairs));
+    PLAN_TRY(cudaMalloc(&p->dc, sizeof(int64_t) * 4));
+    PLAN_TRY(cudaMallocHost(&p->h_dc, sizeof(int64_t) * 4));
+#undef PLAN_TRY
+    s = PASTIS_ERR_CUDA;
+    do {
+        if (cudaMemsetAsync(p->qcodes, 0, (size_t)max_qres + 16, st) != cudaSuccess) break;
+        if (cudaMemsetAsync(p->qoffsets, 0, sizeof(int64_t) * ((size_t)max_q + 1), st) != cudaSuccess) break;
+        if (cudaMemsetAsync(p->dc, 0, sizeof(int64_t) * 4, st) != cudaSuccess) break;
+        // the private context's constants: the matrix and the pass-1 layout
+        int8_t *dmat = (int8_t *)ws_get(p->ctx, WS_FLAGS, 1024);
+        if (!dmat) { s = PASTIS_ERR_OUT_OF_MEMORY; break; }
+        uint8_t hconst[640 + PASTIS_SW_BINS];
+        memcpy(hconst, params->matrix, 576);
+        memset(hconst + 576, 0, 64);
+        memcpy(hconst + 640, p->ctx->sw_lay.extra, PASTIS_SW_BINS);
+        if (cudaMemcpyAsync(dmat, hconst, sizeof(hconst), cudaMemcpyHostToDevice, st) != cudaSuccess) break;
+        align_graph g{p->dc, max_len, max_qres};
+        // a run with every count 0 sizes the workspace, so the capture allocates nothing
+        s = align_qt(p->ctx, p->qcodes, p->qoffsets, max_q, d_tcodes, d_toffsets, n_t, p->pairs, max_pairs,
+                     &p->params, p->out, nullptr, &g);
+        if (s != PASTIS_OK) break;
+        s = PASTIS_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) break;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+        const int64_t launches = p->ctx->launches;
+        pastis_status cs = align_qt(p->ctx, p->qcodes, p->qoffsets, max_q, d_tcodes, d_toffsets, n_t, p->pairs,
+                                    max_pairs, &p->params, p->out, nullptr, &g);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        p->graph = graph;
+        p->ctx->launches = launches;     // counted per replay instead
+        if (cs != PASTIS_OK) { s = cs; break; }
+        if (ce != cudaSuccess || !graph) break;
+        if (cudaGraphInstantiate(&p->exec, graph, 0) != cudaSuccess) break;
+        s = PASTIS_OK;
+    } while (0);
+    if (s != PASTIS_OK) {
+        cudaGetLastError();
+        plan_free(p);
+        return s;
+    }
+    *out = p;
+    return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_align_plan_run(pastis_align_plan *p, const uint8_t *d_qcodes,
+                                               const int64_t *h_qoffsets, int32_t n_q, const pastis_cand *d_pairs,
+                                               int64_t n_pairs, pastis_aln *d_out) {
+    if (!p || !h_qoffsets || n_q < 1 || n_pairs < 0) return PASTIS_ERR_INVALID_ARG;
+    if (h_qoffsets[0] != 0) return PASTIS_ERR_INVALID_ARG;
+    for (int32_t q = 0; q < n_q; ++q)
+        if (h_qoffsets[q + 1] < h_qoffsets[q]) return PASTIS_ERR_INVALID_ARG;
+    if (n_q > p->max_q || n_pairs > p->max_pairs || h_qoffsets[n_q] > p->max_qres) return PASTIS_ERR_CAPACITY;
+    for (int32_t q = 0; q < n_q; ++q)
+        if (h_qoffsets[q + 1] - h_qoffsets[q] > p->max_len) return PASTIS_ERR_CAPACITY;
+    if (n_pairs == 0) return PASTIS_OK;
+    if (!d_pairs || !d_out || (h_qoffsets[n_q] > 0 && !d_qcodes)) return PASTIS_ERR_INVALID_ARG;
+    cudaStream_t st = p->stream;
+    PASTIS_CUDA_TRY(cudaEventRecord(p->ready, p->caller));      // the batch was made on the caller's stream
+    PASTIS_CUDA_TRY(cudaStreamWaitEvent(st, p->ready, 0));
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(p->qoffsets, h_qoffsets, sizeof(int64_t) * ((size_t)n_q + 1),
+                                    cudaMemcpyHostToDevice, st));
+    if (h_qoffsets[n_q] > 0)
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(p->qcodes, d_qcodes, (size_t)h_qoffsets[n_q], cudaMemcpyDeviceToDevice, st));
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(p->pairs, d_pairs, sizeof(pastis_cand) * (size_t)n_pairs,
+                                    cudaMemcpyDeviceToDevice, st));
+    p->h_dc[0] = n_pairs;
+    p->h_dc[1] = h_qoffsets[n_q];
+    p->h_dc[2] = n_q;
+    p->h_dc[3] = 0;
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(p->dc, p->h_dc, sizeof(int64_t) * 4, cudaMemcpyHostToDevice, st));
+    PASTIS_CUDA_TRY(cudaGraphLaunch(p->exec, st));
+    p->ctx->launches++;
+    int hf[6];
+    const int *fl = (const int *)((const int8_t *)p->ctx->ws[WS_FLAGS] + 768);
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(hf, fl, sizeof(hf), cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hf[4]) return PASTIS_ERR_INVALID_ARG;
+    if (hf[5]) return PASTIS_ERR_INVALID_RESIDUE;
+    if (hf[0]) return PASTIS_ERR_INTERNAL;
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(d_out, p->out, sizeof(pastis_aln) * (size_t)n_pairs, cudaMemcpyDeviceToDevice, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    return PASTIS_OK;
+}
+
+extern "C" pastis_status pastis_align_plan_destroy(pastis_align_plan *p) {
+    if (!p) return PASTIS_ERR_INVALID_ARG;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    plan_free(p);
+    return PASTIS_OK;
+}
+
+extern "C" int64_t pastis_align_plan_graph_nodes(const pastis_align_plan *p) {
+    size_t n = 0;
+    if (!p || !p->graph || cudaGraphGetNodes(p->graph, nullptr, &n) != cudaSuccess) return -1;
+    return (int64_t)n;
 }

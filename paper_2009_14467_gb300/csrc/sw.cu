@@ -58,16 +58,21 @@ struct sw_score_out {                      // pass 1 result per pair
 // ---------------------------------------------------------------------------------
 // segments: runs of pairs with the same query, at most SEG_MAX long
 // ---------------------------------------------------------------------------------
-__global__ void k_seg_flags(const pastis_cand *pairs, int64_t n, uint32_t *flags) {
+// dn (captured launches): the pair count in device memory, n the capacity; 0 past it.
+__global__ void k_seg_flags(const pastis_cand *pairs, int64_t n, uint32_t *flags, const int64_t *dn) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    flags[p] = (p == 0 || (p % SEG_MAX) == 0 || pairs[p].i != pairs[p - 1].i) ? 1u : 0u;
+    const int64_t m = dn ? *dn : n;
+    flags[p] = p < m && (p == 0 || (p % SEG_MAX) == 0 || pairs[p].i != pairs[p - 1].i) ? 1u : 0u;
 }
 
-__global__ void k_seg_starts(const uint32_t *flags, const uint32_t *off, int64_t n, int64_t *seg_start) {
+__global__ void k_seg_starts(const uint32_t *flags, const uint32_t *off, int64_t n, int64_t *seg_start,
+                             const int64_t *dn) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n && flags[p]) seg_start[off[p]] = p;
-    if (p == n - 1) seg_start[off[p] + flags[p]] = n;
+    if (p >= n) return;
+    const int64_t m = dn ? *dn : n;
+    if (p < m && flags[p]) seg_start[off[p]] = p;
+    if (p == m - 1) seg_start[off[p] + flags[p]] = m;
 }
 
 // ---------------------------------------------------------------------------------
@@ -446,7 +451,9 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, 
                                                          const pastis_cand *pairs, int64_t n_pairs,
                                                          const int8_t *gmat, int o, int e, const int16_t *bm_all,
                                                          const int64_t *bm_off, unsigned long long *next_pair,
-                                                         sw_score_out *res) {
+                                                         sw_score_out *res, const int64_t *dn, const int *chk) {
+    if (dn) n_pairs = *dn;
+    if (chk && (chk[0] | chk[1])) return;
     __shared__ int s_mat[PASTIS_NSYM * PASTIS_NSYM];
     for (int x = threadIdx.x; x < PASTIS_NSYM * PASTIS_NSYM; x += blockDim.x) s_mat[x] = gmat[x];
     __syncthreads();
@@ -477,9 +484,12 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, 
 }
 
 // Row-pair bound entries of each pair: (query length + 1) / 2.
-__global__ void k_bm_count(const pastis_cand *pairs, int64_t n, const int64_t *qoffsets, int64_t *cnt) {
+__global__ void k_bm_count(const pastis_cand *pairs, int64_t n, const int64_t *qoffsets, int64_t *cnt,
+                           const int64_t *dn, const int *chk) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    // past the batch, or a batch the checks refused (its indexes are not to be followed)
+    if ((dn && p >= *dn) || (chk && (chk[0] | chk[1]))) { cnt[p] = 0; return; }
     const int i = pairs[p].i;
     cnt[p] = (qoffsets[i + 1] - qoffsets[i] + 1) / 2;
 }
@@ -492,7 +502,11 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                                                          size_t warp_bytes, int sstride, int *next_seg,
                                                          int16_t *bm_all, const int64_t *bm_off, sw_score_out *out,
                                                          unsigned long long *cells, const uint8_t *extra,
-                                                         unsigned long long *tune) {
+                                                         unsigned long long *tune, const uint32_t *d_nseg,
+                                                         const int *chk) {
+    // captured launches: the segment count from device memory, nothing on bad input
+    if (d_nseg) n_seg = *d_nseg;
+    if (chk && (chk[0] | chk[1])) return;
     // dynamic shared memory: the profile [NRES][prow_cap] bytes (prow_cap a whole number of stripes)
     extern __shared__ __align__(16) uint8_t s_prof[];
     __shared__ int s_seg, s_next;
@@ -839,7 +853,10 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                                                          const int8_t *gmat, int o, int e, int ani, int cov,
                                                          stripe3_cell *scratch, int sstride, int *next_pair,
                                                          const sw_score_out *res, int score_only, pastis_aln *out,
-                                                         int *err, unsigned long long *cells) {
+                                                         int *err, unsigned long long *cells, const int64_t *dn,
+                                                         const int *chk) {
+    if (dn) n_pairs = *dn;
+    if (chk && (chk[0] | chk[1])) return;
     __shared__ int s_mat[(PASTIS_NSYM + 1) * 32];
     for (int x = threadIdx.x; x < (PASTIS_NSYM + 1) * 32; x += blockDim.x) {
         const int a = x / 32, b = x % 32;
@@ -952,10 +969,13 @@ cudaError_t sw_set_smem_limit(size_t bytes) {
 }
 
 // Host side of the Smith-Waterman path (called by pastis_align_pairs after validation).
+// dn != nullptr: a captured launch sequence (no host synchronisation): n_pairs is the
+// capacity, the pair count is *dn in device memory, the row-pair bounds take their
+// capacity bound, and chk (the input checks' flags) stops the kernels on bad input.
 pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, const uint8_t *d_tcodes,
                        const int64_t *d_toffsets, const pastis_cand *d_pairs,
                        int64_t n_pairs, const pastis_params *p, const int8_t *dmat, int *flags, int lmax,
-                       pastis_aln *d_out, int64_t *d_cells) {
+                       pastis_aln *d_out, int64_t *d_cells, const int64_t *dn, const int *chk) {
     cudaStream_t st = ctx->stream;
     int max_s = 0;
     for (int x = 0; x < PASTIS_NSYM * PASTIS_NSYM; ++x) max_s = std::max(max_s, (int)p->matrix[x]);
@@ -964,27 +984,31 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     PASTIS_WS(sflags, ctx, WS_ALN_ORDER, sizeof(uint32_t) * (2 * (size_t)n_pairs + 2) + sizeof(int64_t) * (n_pairs + 2) + 16);
     uint32_t *soff = sflags + n_pairs + 1;
     int64_t *seg_start = (int64_t *)(((uintptr_t)(soff + n_pairs + 1) + 7) & ~(uintptr_t)7);
-    k_seg_flags<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, sflags);
+    k_seg_flags<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, sflags, dn);
     PASTIS_LAUNCHED(ctx);
     pastis_status s = exclusive_scan_u32(ctx, sflags, soff, n_pairs);
     if (s != PASTIS_OK) return s;
-    k_seg_starts<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(sflags, soff, n_pairs, seg_start);
+    k_seg_starts<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(sflags, soff, n_pairs, seg_start, dn);
     PASTIS_LAUNCHED(ctx);
     uint32_t h_nseg = 0;
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_nseg, soff + n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!dn) {
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_nseg, soff + n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
 
     // row-pair bounds of pass 1 for pass 2: (query length + 1) / 2 int16 per pair
     int64_t *bm_cnt;
     PASTIS_WS(bm_cnt, ctx, WS_ALN_BOFF, sizeof(int64_t) * (2 * (size_t)n_pairs + 1));
     int64_t *bm_off = bm_cnt + n_pairs;
-    k_bm_count<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, bm_cnt);
+    k_bm_count<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_pairs, n_pairs, d_qoffsets, bm_cnt, dn, chk);
     PASTIS_LAUNCHED(ctx);
     s = exclusive_scan_i64(ctx, bm_cnt, bm_off, n_pairs);
     if (s != PASTIS_OK) return s;
-    int64_t h_bm = 0;
-    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_bm, bm_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t h_bm = n_pairs * (int64_t)((lmax + 1) / 2);     // the bound of a captured sequence
+    if (!dn) {
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(&h_bm, bm_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     int16_t *bm_all;
     PASTIS_WS(bm_all, ctx, WS_ALN_BOUND, sizeof(int16_t) * (size_t)h_bm + 16);
 
@@ -1015,7 +1039,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
                                                   p->gap_open, p->gap_extend, max_s, prow_cap, 1u, (char *)scratch,
                                                   warp_bytes, sstride, flags + 1, bm_all, bm_off, res,
                                                   (unsigned long long *)d_cells, (const uint8_t *)dmat + 640,
-                                                  ctx->d_tune);
+                                                  ctx->d_tune, dn ? soff + n_pairs : nullptr, chk);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     const int score_only = p->mode == PASTIS_SW_SCORE;
@@ -1027,7 +1051,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
         k_sw_bound<<<ctx->sm_count * per_sm2, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets,
                                                                    d_pairs, n_pairs, dmat, p->gap_open, p->gap_extend,
                                                                    bm_all, bm_off, (unsigned long long *)(flags + 10),
-                                                                   res);
+                                                                   res, dn, chk);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
     }
@@ -1036,7 +1060,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
                                                p->gap_open,
                                                p->gap_extend, p->ani_min_pct, p->cov_min_pct,
                                                (stripe3_cell *)scratch, sstride, flags + 8, res, score_only, d_out, flags,
-                                               (unsigned long long *)d_cells);
+                                               (unsigned long long *)d_cells, dn, chk);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     return PASTIS_OK;

@@ -345,6 +345,72 @@ def autotune_sw(ctx: Context, codes: torch.Tensor, offsets: torch.Tensor, pairs:
     return extra, cyc
 
 
+def _plan_sigs():
+    L = lib()
+    if not getattr(L, "_plan_sigs", False):
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.pastis_align_plan_create.argtypes = [P, P, P, i32, i32, i64, i64, i32, ctypes.POINTER(c_params),
+                                               ctypes.POINTER(P)]
+        L.pastis_align_plan_create.restype = i32
+        L.pastis_align_plan_run.argtypes = [P, P, P, i32, P, i64, P]
+        L.pastis_align_plan_run.restype = i32
+        L.pastis_align_plan_destroy.argtypes = [P]
+        L.pastis_align_plan_destroy.restype = i32
+        L.pastis_align_plan_graph_nodes.argtypes = [P]
+        L.pastis_align_plan_graph_nodes.restype = i64
+        L._plan_sigs = True
+    return L
+
+
+class AlignPlan:
+    """pastis_align_plan: the alignment of a batch of queries against resident targets,
+    captured once as a CUDA graph over buffers of fixed capacity and replayed per batch
+    (one graph launch per run).  Runs on ctx's stream."""
+
+    def __init__(self, ctx: Context, tcodes: torch.Tensor, toffsets: torch.Tensor, params: Params,
+                 max_q: int, max_qres: int, max_pairs: int, max_len: int):
+        L = _plan_sigs()
+        self._targets = (tcodes, toffsets)          # the plan reads them on every run
+        self.max_q, self.max_qres, self.max_pairs, self.max_len = max_q, max_qres, max_pairs, max_len
+        p = params.c()
+        h = ctypes.c_void_p()
+        _check("pastis_align_plan_create", L.pastis_align_plan_create(
+            ctx.h, _ptr(tcodes), _ptr(toffsets), toffsets.numel() - 1, max_q, max_qres, max_pairs, max_len,
+            ctypes.byref(p), ctypes.byref(h)))
+        self.h = h
+        self.device = tcodes.device
+
+    def fits(self, qoffsets_host: np.ndarray, n_pairs: int) -> bool:
+        n_q = qoffsets_host.shape[0] - 1
+        return (1 <= n_q <= self.max_q and n_pairs <= self.max_pairs and int(qoffsets_host[-1]) <= self.max_qres
+                and int(np.diff(qoffsets_host).max(initial=0)) <= self.max_len)
+
+    def run(self, qcodes: torch.Tensor, qoffsets_host: np.ndarray, pairs: torch.Tensor,
+            out: torch.Tensor = None) -> torch.Tensor:
+        """pastis_align_plan_run: one record (uint8 [n, 20]) per pair."""
+        qo = np.ascontiguousarray(qoffsets_host, dtype=np.int64)
+        n = pairs.shape[0]
+        out = torch.empty((max(n, 1), REC_BYTES), dtype=torch.uint8, device=self.device) if out is None else out
+        _check("pastis_align_plan_run", _plan_sigs().pastis_align_plan_run(
+            self.h, _ptr(qcodes), qo.ctypes.data_as(ctypes.c_void_p), qo.shape[0] - 1, _ptr(pairs), n, _ptr(out)))
+        return out[:n]
+
+    @property
+    def graph_nodes(self) -> int:
+        return int(_plan_sigs().pastis_align_plan_graph_nodes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _plan_sigs().pastis_align_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def filter_edges(ctx: Context, offsets: torch.Tensor, pairs: torch.Tensor, alns: torch.Tensor,
                  params: Params) -> torch.Tensor:
     """pastis_filter_edges: edges (uint8 [n, 20]) of the pairs that pass, in pair order."""

@@ -9,8 +9,11 @@ it (admission by free device memory), so requests that arrive while others run a
 admitted as slots and memory free up, and their kernels overlap on the GPU.  Each
 request runs the hot path in serving form: encode -> query k-mer matrix -> query x
 database candidates -> (optional learned prefilter) -> alignment -> filter, and
-returns the edges (query index, database index, ident, cols, score, ANI).  Every
-numeric step is a library kernel; this module only schedules.
+returns the edges (query index, database index, ident, cols, score, ANI).  Each
+worker's alignment of a request within the plan's capacities is one replay of a CUDA
+graph captured at the worker's start (pastis_align_plan); larger requests take the
+direct call, with the same records.  Every numeric step is a library kernel; this
+module only schedules.
 """
 import concurrent.futures
 import ctypes
@@ -44,7 +47,8 @@ class Server:
     """Query batches against a resident database."""
 
     def __init__(self, db_ascii: np.ndarray, db_offsets: np.ndarray, params: P.Params, device: int = 0,
-                 slots: int = 4, reserve_bytes: int = 8 << 30, prefilter=None):
+                 slots: int = 4, reserve_bytes: int = 8 << 30, prefilter=None, graphs: bool = True,
+                 graph_pairs: int = 1 << 20, graph_queries: int = 4096, graph_residues: int = 4 << 20):
         if params.m_subs != 0:
             raise ValueError("the serving form takes exact k-mers (m_subs = 0)")
         self.params = params
@@ -62,6 +66,12 @@ class Server:
             build_stream.synchronize()
             ctx.close()
         self.n_db = int(db_offsets.shape[0] - 1)
+        # alignment plans (CUDA graphs), one per worker context, for requests within
+        # their capacities; longer queries or more pairs take the direct call
+        self.graphs = graphs
+        self.graph_caps = (graph_queries, graph_residues, graph_pairs,
+                           max(2000, int(np.diff(db_offsets).max(initial=0))))
+        self.graph_runs = 0
         self.q = queue.Queue()
         self.mem_lock = threading.Lock()
         self.in_flight_bytes = 0
@@ -111,15 +121,38 @@ class Server:
             net, thr = self.prefilter
             z = F.forward(ctx, net, F.features_qt(ctx, codes, o, self.db_codes, self.db_offsets, cands, self.params))
             cands = F.select(ctx, cands, z, thr)
-        alns = align_pairs_qt(ctx, codes, o, self.db_codes, self.db_offsets, cands, self.params)
+        plan = self._plan(ctx) if self.graphs else None
+        if plan is not None and plan.fits(r.offsets, cands.shape[0]):
+            alns = plan.run(codes, r.offsets, cands)
+            self.graph_runs += 1
+        else:
+            alns = align_pairs_qt(ctx, codes, o, self.db_codes, self.db_offsets, cands, self.params)
         edges = filter_edges_qt(ctx, o, self.db_offsets, cands, alns, self.params)
         return P.to_records(edges, P.EDGE_DTYPE)
+
+    def _plan(self, ctx: P.Context):
+        """The context's plan for this server (made on first use, kept on the context)."""
+        plan = getattr(ctx, "_serve_plan", None)
+        if plan is None or plan[0] is not self:
+            q, res, pairs, ln = self.graph_caps
+            plan = (self, P.AlignPlan(ctx, self.db_codes, self.db_offsets, self.params, q, res, pairs, ln))
+            ctx._serve_plan = plan
+        return plan[1]
+
+    def drop_plan(self, ctx: P.Context):
+        """Frees the context's plan (before the context closes)."""
+        plan = getattr(ctx, "_serve_plan", None)
+        if plan is not None:
+            plan[1].close()
+            ctx._serve_plan = None
 
     def _worker(self, slot: int):
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(self.device)
         with torch.cuda.stream(stream):
             ctx = P.Context(self.device.index or 0, stream)
+            if self.graphs:
+                self._plan(ctx)             # captured before the first request
             while True:
                 r = self.q.get()
                 if r is None:
@@ -148,6 +181,7 @@ class Server:
                 finally:
                     with self.mem_lock:
                         self.in_flight_bytes -= need
+            self.drop_plan(ctx)
             ctx.close()
 
 
