@@ -272,7 +272,7 @@ __device__ __forceinline__ int band_get(const int (&X)[2], int idx, bool wide) {
     return (unsigned)idx < (wide ? 64u : 32u) ? v : NEG;
 }
 
-__device__ bool band_walk(const uint8_t *__restrict__ q, const uint8_t *__restrict__ t, const int *s_mat, int o,
+__device__ __noinline__ bool band_walk(const uint8_t *__restrict__ q, const uint8_t *__restrict__ t, const int *s_mat, int o,
                           int e, int S, int ei, int ej, const int16_t *__restrict__ bm, int *amax_out,
                           int *bmax_out) {
     const int lane = threadIdx.x & 31;
@@ -446,7 +446,7 @@ __device__ bool band_rows(const uint8_t *__restrict__ q, const uint8_t *__restri
 }
 
 // Pass 2 over every pair pass 1 scored: one warp per pair, a few pairs per grab.
-__global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, const int64_t *qoffsets,
+__global__ void __launch_bounds__(SW_THREADS, 5) k_sw_bound(const uint8_t *qcodes, const int64_t *qoffsets,
                                                          const uint8_t *tcodes, const int64_t *toffsets,
                                                          const pastis_cand *pairs, int64_t n_pairs,
                                                          const int8_t *gmat, int o, int e, const int16_t *bm_all,
@@ -458,26 +458,42 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_bound(const uint8_t *qcodes, 
     for (int x = threadIdx.x; x < PASTIS_NSYM * PASTIS_NSYM; x += blockDim.x) s_mat[x] = gmat[x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    constexpr int GRAB = 4;
+    constexpr int GRAB = 8;
     for (;;) {
         unsigned long long g = 0;
         if (lane == 0) g = atomicAdd(next_pair, (unsigned long long)GRAB);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= (unsigned long long)n_pairs) break;
+        // lane u < GRAB fetches pair g + u's pass-1 result, sequences and bounds, so the
+        // grab's load chains run side by side instead of one after the other
+        int ok_l = 0, sc_l = 0, ei_l = 0, ej_l = 0;
+        int64_t qo_l = 0, to_l = 0, bo_l = 0;
+        const int64_t pl = (int64_t)g + lane;
+        if (lane < GRAB && pl < n_pairs) {
+            const sw_score_out r = res[pl];
+            if (!r.big && r.score > 0) {
+                const pastis_cand c = pairs[pl];
+                qo_l = qoffsets[c.i];
+                to_l = toffsets[c.j];
+                bo_l = bm_off[pl];
+                sc_l = r.score; ei_l = r.end_i; ej_l = r.end_j;
+                ok_l = 1;
+            }
+        }
         for (int u = 0; u < GRAB; ++u) {
+            if (!__shfl_sync(0xffffffffu, ok_l, u)) continue;
             const int64_t p = (int64_t)g + u;
-            if (p >= n_pairs) break;
-            const sw_score_out r = res[p];
-            if (r.big || r.score <= 0) continue;
-            const pastis_cand c = pairs[p];
+            const int score = __shfl_sync(0xffffffffu, sc_l, u);
+            const int ei = __shfl_sync(0xffffffffu, ei_l, u), ej = __shfl_sync(0xffffffffu, ej_l, u);
+            const uint8_t *qp = qcodes + __shfl_sync(0xffffffffu, qo_l, u);
+            const uint8_t *tp = tcodes + __shfl_sync(0xffffffffu, to_l, u);
+            const int16_t *bm = bm_all + __shfl_sync(0xffffffffu, bo_l, u);
             int amax = 0, bmax = 0;
-            const uint8_t *qp = qcodes + qoffsets[c.i], *tp = tcodes + toffsets[c.j];
-            const int16_t *bm = bm_all + bm_off[p];
-            bool ok = o >= e && band_rows(qp, tp, s_mat, o, e, r.score, r.end_i, r.end_j, bm, &amax, &bmax);
-            if (!ok) ok = band_walk(qp, tp, s_mat, o, e, r.score, r.end_i, r.end_j, bm, &amax, &bmax);
+            bool ok = o >= e && band_rows(qp, tp, s_mat, o, e, score, ei, ej, bm, &amax, &bmax);
+            if (!ok) ok = band_walk(qp, tp, s_mat, o, e, score, ei, ej, bm, &amax, &bmax);
             if (ok && amax > 0 && bmax > 0 && lane == 0) {
-                res[p].rect_i = r.end_i + 1 - amax;
-                res[p].rect_j = r.end_j + 1 - bmax;
+                res[p].rect_i = ei + 1 - amax;
+                res[p].rect_j = ej + 1 - bmax;
             }                                      // else: the whole up-left rectangle (0, 0)
         }
     }
