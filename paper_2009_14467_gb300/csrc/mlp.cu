@@ -1,6 +1,6 @@
 // Learned prefilter: a 16 -> 256 -> 256 -> 1 MLP over per-pair features that predicts
 // whether a candidate pair's alignment will pass the similarity filter (Sec. IV-F), so
-// that pairs predicted to fail skip the alignment.  The exact path stays the judge:
+// that pairs predicted to fail skip the alignment.  The exact path stays the reference:
 // labels come from it, and the kept fraction and edge recall are measured against it.
 // (The paper's own lever for fewer alignments is the common-k-mer threshold, Sec. VI,
 // which costs 2-3% recall; this is a learned version of the same trade.)

@@ -21,8 +21,9 @@
 //   Queries longer than one stripe of 32 * 16 rows go in stripes whose last row is
 //   handed on through a per-warp buffer.
 // Pass 2 (its own kernel, one warp per pair; a band around the path): an anchored DP
-//   over the reversed prefixes from the end (ei, ej), each lane holding up to two cells
-//   of an antidiagonal.  A suffix of the traced path starting on row i scores S minus
+//   over the reversed prefixes from the end (ei, ej), row by row with up to 64 columns
+//   per row (two per lane; antidiagonal by antidiagonal when a row needs more or the
+//   gap costs have o < e).  A suffix of the traced path starting on row i scores S minus
 //   the forward value before it, which is at most the largest H pass 1 met on row
 //   i-1's pair of rows; cells below that threshold die, the path's suffixes all
 //   survive, and the cells reaching S bound the begin.  Their extent gives a rectangle
@@ -32,9 +33,12 @@
 //   traceback would take.  Inside a rectangle holding the path, the path's cells keep
 //   their values and every choice along it is the same, so the carry at the end cell
 //   is the traceback's.  cols = span_q + span_t - matched.
-// Pairs whose scores could reach SCORE_MAX (max score * shorter length), gap costs
-// with o + e > GAP_MAX, and queries longer than the shared-memory profile take pass 3
-// over the whole matrix with the end tracked there instead (int32).
+// Pairs whose scores could reach SCORE_MAX (max score * shorter length), gap opens
+// above GAP_MAX, and queries longer than the shared-memory profile take pass 3 over the
+// whole matrix with the end tracked there instead (int32).
+// Captured launch sequences (alignment plans) pass device-side counts: each kernel then
+// reads its pair or segment count from device memory and does nothing when the input
+// checks flagged the batch.
 #include <algorithm>
 
 #include "internal.cuh"

@@ -4,7 +4,7 @@ pastis_prefilter_select and the training driver around them.
 Every numeric step (features, forward, backward, Adam, selection) runs in the library's
 kernels; this module allocates the caller-owned parameter buffers with torch, sequences
 the calls and picks the decision threshold.  Labels come from the exact path (the
-`passes` verdict of pastis_align_pairs), which also stays the judge of edge recall.
+`passes` verdict of pastis_align_pairs), against which edge recall is also measured.
 """
 import ctypes
 import math
