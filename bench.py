@@ -762,22 +762,31 @@ def main():
     # end to end through the public API from pinned host buffers (H2D + path + D2H)
     torch.cuda.synchronize()
     barrier()
+    # the same row blocks as the timed steps, so both numbers cover the same work
     e2e_ms = []
     h2d = ascii_host.numel() + offs_host.numel() * 8
     d2h = 0
-    for _ in range(max(1, min(args.steps, 2))):
+    e2e_edges = 0
+    n_e2e = max(1, min(args.steps, 2))
+    for k in range(n_e2e):
         flush.fill_(1)
         torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         a = ascii_host.to(dev, non_blocking=True)
         o = offs_host.to(dev, non_blocking=True)
-        r = P.run(ctx, a, o, params, rows=blocks[counter[0] % batches])
-        counter[0] += 1
+        r = P.run(ctx, a, o, params, rows=blocks[(args.warmup + k) % batches])
         edges_host = r["edges"].to("cpu")
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
+        e2e_edges += edges_host.shape[0]
         d2h = edges_host.numel()
-    e2e_value = edges_host.shape[0] * world / (max(e2e_ms) / 1000.0)
+    e2e_t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+    e2e_e = torch.tensor([float(e2e_edges)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)      # the slowest rank's time
+        dist.all_reduce(e2e_e, op=dist.ReduceOp.SUM)      # every rank's edges
+    e2e_value = float(e2e_e.item()) / (float(e2e_t.item()) / 1000.0)
 
     # roofline of the dominant kernel: SW pass 1 (integer ALU bound)
     roof = None
