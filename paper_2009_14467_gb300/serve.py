@@ -27,6 +27,17 @@ import torch
 from . import pastis as P
 
 
+ADMIT_WAIT_S = 30.0
+
+
+def admissible(free: int, in_flight: int, reserve: int, need: int, waited: float) -> bool:
+    """Admission by device memory: a request starts when the free memory, less what the
+    requests already admitted may still take and a reserve, covers its estimate; always
+    when nothing else is in flight (it cannot wait for memory nobody will free), and
+    after waiting ADMIT_WAIT_S (so that an estimate set too high cannot stall it)."""
+    return free - in_flight - reserve >= need or in_flight == 0 or waited > ADMIT_WAIT_S
+
+
 class Request:
     def __init__(self, ascii_host: np.ndarray, offsets_host: np.ndarray, rid: int):
         self.ascii = ascii_host
@@ -162,8 +173,7 @@ class Server:
                 while True:               # admission by free device memory (bounded wait)
                     with self.mem_lock:
                         free, _ = torch.cuda.mem_get_info(self.device)
-                        if free - self.in_flight_bytes - self.reserve >= need or self.in_flight_bytes == 0 \
-                                or waited > 30.0:
+                        if admissible(free, self.in_flight_bytes, self.reserve, need, waited):
                             self.in_flight_bytes += need
                             break
                     time.sleep(0.002)
