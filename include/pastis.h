@@ -13,6 +13,15 @@
  *   pastis_align_pairs       Smith-Waterman or x-drop alignment       (Sec. IV-E)
  *   pastis_filter_edges      ANI / coverage filter -> edges           (Sec. IV-F, VI-B)
  *
+ * Around it: the row-block form of the product (pastis_overlap_spgemm_rows); the
+ * serving form against a resident database (pastis_query_overlap,
+ * pastis_align_pairs_qt, pastis_filter_edges_qt); batching (the pass-1 layout and its
+ * tuner, pastis_sw_layout_*, pastis_autotune_sw; alignment plans replayed as CUDA
+ * graphs, pastis_align_plan_*); a learned prefilter (pastis_pair_features*,
+ * pastis_mlp_*, pastis_prefilter_select); the graph variants of Sec. VI-B
+ * (PASTIS_SW_SCORE, pastis_ns_edges, pastis_components); a filter that allocates
+ * nothing (pastis_filter_edges_static); and the context's profiler and counters.
+ *
  * Conventions shared by every call:
  *  - Every pointer named d_* is DEVICE memory owned by the caller; h_* is host
  *    memory.  The library never frees caller memory.  It owns only the workspace
