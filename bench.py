@@ -522,7 +522,8 @@ def run_serve(args):
         ctx.close()
         pref = {"net": net, "threshold": thr, "train_pairs": n_train, "train_s": train_s,
                 "calibration": f"threshold {thr:.4f} for recall {args.calib_recall} on 1,500 calibration queries"}
-    srv = S.Server(db.ascii, db.offsets, params, slots=args.slots, reserve_bytes=8 << 30)
+    srv = S.Server(db.ascii, db.offsets, params, slots=args.slots, reserve_bytes=8 << 30,
+                   chunk_queries=args.chunk_queries)
     # warm-up, then the batch path: every request in turn on one slot, nothing overlapping
     for q in reqs[:3]:
         srv.submit(q.ascii, q.offsets).future.result()
@@ -578,7 +579,7 @@ def run_serve(args):
     if pref is not None:
         # the same stream through the prefilter: latency, throughput and edge recall
         srv = S.Server(db.ascii, db.offsets, params, slots=args.slots, reserve_bytes=8 << 30,
-                       prefilter=(pref["net"], pref["threshold"]))
+                       prefilter=(pref["net"], pref["threshold"]), chunk_queries=args.chunk_queries)
         for q in reqs[:3]:
             srv.submit(q.ascii, q.offsets).future.result()
         ctx = P.Context(0)
@@ -614,7 +615,7 @@ def run_serve(args):
             "config": {"workload": f"database: {w['desc']}; exact k-mers (m = 0)", "name": name,
                        "requests": len(reqs), "request_sizes": "log-uniform 1..4096 queries",
                        "arrivals": f"Poisson, {rate:.3f} requests/s (70% of batch capacity)",
-                       "slots": args.slots},
+                       "slots": args.slots, "chunk_queries": args.chunk_queries},
             "p50_s": st["p50_s"], "p99_s": st["p99_s"], "queries": nq,
             "batch_path_queries_per_s": cap, "edges": n_edges, "edges_batch_path": n_edges_batch,
             "graphs": graphs, "prefiltered": pf}
@@ -647,6 +648,8 @@ def main():
     ap.add_argument("--prefilter", action="store_true",
                     help="serve mode: also run the stream through the learned prefilter")
     ap.add_argument("--no-graphs", action="store_true", help="serve mode: direct alignment calls, no CUDA graphs")
+    ap.add_argument("--chunk-queries", type=int, default=0,
+                    help="serve mode: run requests above this many queries as chunks in rounds (0: whole)")
     ap.add_argument("--recall", type=float, default=0.995, help="edge recall the prefilter must keep")
     ap.add_argument("--calib-recall", type=float, default=0.998,
                     help="recall the threshold is calibrated for on the calibration block (margin over --recall)")

@@ -9,7 +9,10 @@ it (admission by free device memory), so requests that arrive while others run a
 admitted as slots and memory free up, and their kernels overlap on the GPU.  Each
 request runs the hot path in serving form: encode -> query k-mer matrix -> query x
 database candidates -> (optional learned prefilter) -> alignment -> filter, and
-returns the edges (query index, database index, ident, cols, score, ANI).  Each
+returns the edges (query index, database index, ident, cols, score, ANI).  With
+`chunk_queries` > 0 a larger request runs as chunks of consecutive queries that the
+slots take like requests of their own, in rounds across requests, its edges joined in
+query order.  Each
 worker's alignment of a request within the plan's capacities is one replay of a CUDA
 graph captured at the worker's start (pastis_align_plan); larger requests take the
 direct call, with the same records.  Every numeric step is a library kernel; this
@@ -17,6 +20,7 @@ module only schedules.
 """
 import concurrent.futures
 import ctypes
+import itertools
 import queue
 import threading
 import time
@@ -38,6 +42,14 @@ def admissible(free: int, in_flight: int, reserve: int, need: int, waited: float
     return free - in_flight - reserve >= need or in_flight == 0 or waited > ADMIT_WAIT_S
 
 
+def query_chunks(n: int, chunk: int):
+    """Query ranges [c0, c1) of at most `chunk` queries covering [0, n), in order."""
+    if chunk <= 0 or n <= chunk:
+        return [(0, n)]
+    k = -(-n // chunk)
+    return [(n * x // k, n * (x + 1) // k) for x in range(k)]
+
+
 class Request:
     def __init__(self, ascii_host: np.ndarray, offsets_host: np.ndarray, rid: int):
         self.ascii = ascii_host
@@ -48,6 +60,10 @@ class Request:
         self.t_start = None
         self.t_done = None
         self.future = concurrent.futures.Future()
+        self.parent = None                  # a chunk: (request, chunk index, first query)
+        self.parts = None                   # a split request: its chunks' edges
+        self.left = 0
+        self.lock = threading.Lock()
 
 
 def _kmat_c(A):
@@ -59,7 +75,8 @@ class Server:
 
     def __init__(self, db_ascii: np.ndarray, db_offsets: np.ndarray, params: P.Params, device: int = 0,
                  slots: int = 4, reserve_bytes: int = 8 << 30, prefilter=None, graphs: bool = True,
-                 graph_pairs: int = 1 << 20, graph_queries: int = 4096, graph_residues: int = 4 << 20):
+                 graph_pairs: int = 1 << 20, graph_queries: int = 4096, graph_residues: int = 4 << 20,
+                 chunk_queries: int = 0):
         if params.m_subs != 0:
             raise ValueError("the serving form takes exact k-mers (m_subs = 0)")
         self.params = params
@@ -83,7 +100,16 @@ class Server:
         self.graph_caps = (graph_queries, graph_residues, graph_pairs,
                            max(2000, int(np.diff(db_offsets).max(initial=0))))
         self.graph_runs = 0
-        self.q = queue.Queue()
+        # optional: a request of more than chunk_queries queries runs as chunks that the
+        # slots take independently, so small requests need not wait behind a large one
+        # and a large one spreads over the slots; the chunks' edges are joined in query
+        # order (the same edges).  0 (the default): whole requests, first come first served
+        self.chunk_queries = chunk_queries
+        # the slots take work in rounds: every request's first chunk before any request's
+        # second (arrival order within a round), so a large request does not hold back the
+        # requests that arrive after it
+        self.q = queue.PriorityQueue()
+        self.seq = itertools.count()
         self.mem_lock = threading.Lock()
         self.in_flight_bytes = 0
         self.stop = False
@@ -95,13 +121,53 @@ class Server:
     # -- public --------------------------------------------------------------------
     def submit(self, ascii_host: np.ndarray, offsets_host: np.ndarray, rid: int = 0) -> Request:
         r = Request(ascii_host, offsets_host, rid)
-        self.q.put(r)
+        ranges = query_chunks(r.n, self.chunk_queries)
+        if len(ranges) == 1:
+            self.q.put((0, next(self.seq), r))
+            return r
+        r.parts = [None] * len(ranges)
+        r.left = len(ranges)
+        for x, (c0, c1) in enumerate(ranges):
+            o0, o1 = int(offsets_host[c0]), int(offsets_host[c1])
+            c = Request(ascii_host[o0:o1], np.ascontiguousarray(offsets_host[c0:c1 + 1] - o0), rid)
+            c.t_submit = r.t_submit
+            c.parent = (r, x, c0)
+            self.q.put((x, next(self.seq), c))
         return r
+
+    def _finish(self, r: Request, res=None, exc=None):
+        """Completes a request, or a chunk and, with its last chunk, its request."""
+        r.t_done = time.perf_counter()
+        if r.parent is None:
+            if exc is not None:
+                r.future.set_exception(exc)
+            else:
+                self.done.append(r)
+                r.future.set_result(res)
+            return
+        top, x, c0 = r.parent
+        with top.lock:
+            if exc is not None:
+                top.parts[x] = exc
+            else:
+                res = res.copy()
+                res["i"] += c0
+                top.parts[x] = res
+            top.left -= 1
+            last = top.left == 0
+        if last:
+            top.t_done = time.perf_counter()
+            bad = [p for p in top.parts if isinstance(p, BaseException)]
+            if bad:
+                top.future.set_exception(bad[0])
+            else:
+                self.done.append(top)
+                top.future.set_result(np.concatenate(top.parts))
 
     def close(self):
         self.stop = True
         for _ in self.workers:
-            self.q.put(None)
+            self.q.put((float("inf"), next(self.seq), None))
         for w in self.workers:
             w.join(timeout=60)
 
@@ -165,7 +231,7 @@ class Server:
             if self.graphs:
                 self._plan(ctx)             # captured before the first request
             while True:
-                r = self.q.get()
+                r = self.q.get()[2]
                 if r is None:
                     break
                 need = self.estimate_bytes(r)
@@ -182,12 +248,9 @@ class Server:
                 try:
                     res = self.process(ctx, r)
                     stream.synchronize()
-                    r.t_done = time.perf_counter()
-                    self.done.append(r)
-                    r.future.set_result(res)
+                    self._finish(r, res=res)
                 except Exception as exc:       # the request fails, the server keeps going
-                    r.t_done = time.perf_counter()
-                    r.future.set_exception(exc)
+                    self._finish(r, exc=exc)
                 finally:
                     with self.mem_lock:
                         self.in_flight_bytes -= need

@@ -114,3 +114,22 @@ def test_serving_with_prefilter_alone_equals_mixed(server):
         kept += len(a)
         total += len(x)
     assert 0 < kept <= total
+
+
+def test_chunked_requests_equal_whole_requests(server):
+    # requests split into chunks of 7 queries give the unsplit server's edges, alone
+    # and all at once
+    P, srv, db, reqs = server
+    from paper_2009_14467_gb300 import serve as S
+    whole = [srv.submit(q.ascii, q.offsets, 300 + r).future.result(timeout=300) for r, q in enumerate(reqs)]
+    small = S.Server(db.ascii, db.offsets, P.Params(matrix=MAT), slots=3, reserve_bytes=1 << 30, chunk_queries=7)
+    try:
+        alone = [small.submit(q.ascii, q.offsets, r).future.result(timeout=300) for r, q in enumerate(reqs)]
+        handles = [small.submit(q.ascii, q.offsets, 100 + r) for r, q in enumerate(reqs)]
+        mixed = [h.future.result(timeout=300) for h in handles]
+        st = small.latency_stats()
+    finally:
+        small.close()
+    for w, a, m in zip(whole, alone, mixed):
+        assert a.tobytes() == w.tobytes() and m.tobytes() == w.tobytes()
+    assert st["requests"] == 2 * len(reqs)                 # one entry per request, not per chunk

@@ -75,3 +75,17 @@ def test_serving_admission_by_memory():
     assert not admissible(free=40 * G, in_flight=20 * G, reserve=8 * G, need=20 * G, waited=0.0)
     assert admissible(free=1 * G, in_flight=0, reserve=8 * G, need=20 * G, waited=0.0)      # alone
     assert admissible(free=1 * G, in_flight=5 * G, reserve=8 * G, need=20 * G, waited=ADMIT_WAIT_S + 0.01)
+
+
+@pytest.mark.parametrize("n,chunk", [(1, 512), (512, 512), (513, 512), (4096, 512), (1000, 7), (10, 0)])
+def test_serving_query_chunks_cover_in_order(n, chunk):
+    from paper_2009_14467_gb300.serve import query_chunks
+    r = query_chunks(n, chunk)
+    assert r[0][0] == 0 and r[-1][1] == n
+    assert all(a[1] == b[0] for a, b in zip(r, r[1:]))            # contiguous, in order
+    sizes = [c1 - c0 for c0, c1 in r]
+    assert min(sizes) >= 1
+    if chunk > 0:
+        assert max(sizes) <= chunk and max(sizes) - min(sizes) <= 1
+    else:
+        assert r == [(0, n)]
