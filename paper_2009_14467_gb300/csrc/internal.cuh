@@ -16,8 +16,8 @@ enum ws_slot {
     WS_KMER_TMP,
     WS_SUB_ROOTS, WS_SUB_CODE, WS_SUB_DIST,
     WS_AS_ROWPTR, WS_AS_CODE, WS_AS_POS, WS_AS_COLPTR, WS_AS_COLSEQ, WS_AS_COLPOS,
-    WS_AS_TMP_KEY, WS_AS_TMP_VAL,
-    WS_SPG_ROWWORK, WS_SPG_ROWOFF, WS_SPG_ROWCNT, WS_SPG_TMP, WS_SPG_TABLE, WS_SPG_BIN,
+    WS_AS_TMP_KEY,
+    WS_SPG_ROWWORK, WS_SPG_ROWOFF, WS_SPG_TMP, WS_SPG_CURSORS, WS_SPG_BIN,
     WS_SPG_RESULT,
     WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER, WS_ALN_BOUND, WS_ALN_BOFF,
     WS_FILT_FLAGS, WS_FILT_SCAN, WS_CC,

@@ -442,7 +442,7 @@ static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const p
     int64_t *d_nact = d_eoff + ni;
     int64_t *d_nprod = d_nact + ni;
     char *cbuf;
-    PASTIS_WS(cbuf, ctx, WS_SPG_TABLE, (sizeof(int32_t) * 2 + sizeof(int64_t) * 2) * (size_t)n_ent + 64);
+    PASTIS_WS(cbuf, ctx, WS_SPG_CURSORS, (sizeof(int32_t) * 2 + sizeof(int64_t) * 2) * (size_t)n_ent + 64);
     cur.x = (int64_t *)cbuf;
     cur.pe = cur.x + n_ent;
     cur.nj = (int32_t *)(cur.pe + n_ent);
