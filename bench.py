@@ -38,7 +38,7 @@ OPS_PER_CELL = 11          # integer ops per SW cell: E 3, F 3, H 4, running bes
 INT_LANES_PER_SM = 128     # 32-bit integer lanes per SM per clock
 HALVES_PER_LANE = 2        # SW pass 1 works on 16-bit halves, two per 32-bit lane op
 N_SM = 152
-SW1_DRAM_BYTES_PER_PAIR = 546.7e6 / 1_086_756
+SW1_DRAM_BYTES_PER_PAIR = 547_332_608 / 1_086_756
 
 WORKLOADS = {
     "zipf_100k_s25_sw": dict(n=100_000, m=25, mode=0, desc=(
@@ -801,7 +801,7 @@ def main():
         sm_max = (clk or {}).get("sm_max_mhz", 2070.0) or 2070.0
         peak = N_SM * INT_LANES_PER_SM * HALVES_PER_LANE * sm_max * 1e6 / 1e12
         # DRAM bytes per launch: the ncu capture of this kernel on the 5,000-protein set of
-        # the same recipe measured 546.7 MB for 1,086,756 pairs (the per-row-pair maxima
+        # the same recipe measured 547.3 MB for 1,086,756 pairs (the per-row-pair maxima
         # written for pass 2, which grow with the pairs), scaled by the launch's pairs
         traffic = SW1_DRAM_BYTES_PER_PAIR * cands_total / max(1, args.steps) if w["mode"] == 0 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
