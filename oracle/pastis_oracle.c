@@ -20,9 +20,12 @@
  *   or_components      connected components of the edge graph    Sec. VI-B (components)
  *
  * Readings where the paper is silent are stated beside the code that takes them.
- * Parity unpinned: the pruning order inside or_xd and the symmetrization rule inside
- * or_candidates are definitions of this oracle (the paper gives neither); everything
- * else is pinned by the tests against brute force, closed forms and printed values.
+ * Two of them are definitions the paper does not give at all: the pruning order inside
+ * or_xd (the paper hands x-drop to SeqAn) and the symmetrization rule inside
+ * or_candidates.  The tests pin both to the reading stated here with cases worked out
+ * by hand (every antidiagonal of small gapped extensions, the seed choice in each of its
+ * branches, both orientations of a substitute pair) and with brute force; everything else
+ * is pinned against brute force, closed forms and the values the paper prints.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -624,6 +627,8 @@ static int passes(const span_stats *s, int32_t lq, int32_t lt, int32_t ani, int3
 /* seeds and keeps the best alignment that passes the filter.  Reading: among   */
 /* passing seeds the higher score wins, the first seed on a tie; when none     */
 /* passes, the best score is reported (first seed on a tie) with passes = 0.    */
+/* Mode 3 is SW for the filter of Sec. IV-F only: a pair that fails keeps its   */
+/* score and end, and its begin, identities and columns are reported as 0.      */
 int or_align_pairs(const uint8_t *codes, const int64_t *offsets, const or_cand *pairs,
                    int64_t n_pairs, const int8_t *mat, int32_t o, int32_t e, int32_t mode,
                    int32_t X, int32_t k, int32_t ani, int32_t cov, or_aln *out, int64_t *cells) {
@@ -634,10 +639,14 @@ int or_align_pairs(const uint8_t *codes, const int64_t *offsets, const or_cand *
         int32_t lt = (int32_t)(offsets[c->j + 1] - offsets[c->j]);
         span_stats best;
         int used = 0, ok = 0;
-        if (mode == 0 || mode == 2) {
+        if (mode == 0 || mode == 2 || mode == 3) {
             or_sw(q, lq, t, lt, mat, o, e, &best);
             if (cells) *cells += (int64_t)lq * lt;
             ok = passes(&best, lq, lt, ani, cov);
+            if (mode == 3 && !ok) {
+                best.qb = best.tb = 0;
+                best.ident = best.cols = 0;
+            }
             if (mode == 2) {
                 /* score and end only (what the NS weight needs, Sec. VI-B: no traceback) */
                 best.qb = best.tb = 0;

@@ -1,5 +1,7 @@
 """Pins for the oracle's Smith-Waterman, x-drop and filter: brute-force enumeration of
 every alignment on short sequences, closed forms and invariants."""
+import os
+
 import numpy as np
 import pytest
 
@@ -224,3 +226,75 @@ def test_filter_uses_shorter_sequence():
     alns[1] = (50, 0, 150, 0, 69, 30, 80, 0, 0, 0)     # 69/100 on j: vetoed
     e = O.filter_edges(offs, pairs, alns)
     assert len(e) == 1
+
+
+
+# ---- hand-worked x-drop cases (pruning with gaps, seed choice) ----------------------
+
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "xdrop_worked.txt")
+
+
+def _golden_matrix(name):
+    """The scoring matrices the worked cases name (defined in the golden file)."""
+    m = np.zeros((24, 24), np.int8)
+    if name == "unit2":
+        m[:] = -2
+        np.fill_diagonal(m, 2)
+    elif name == "cw":
+        m[:] = -6
+        for ch, v in (("C", 11), ("A", 4), ("D", 4), ("E", 4)):
+            m[A.index(ch), A.index(ch)] = v
+    else:
+        raise ValueError(name)
+    return m
+
+
+def _golden_xd_cases():
+    cases = []
+    with open(_GOLDEN) as f:
+        for line in f:
+            tok = line.split("#", 1)[0].split()
+            if not tok:
+                continue
+            assert tok[0] == "xd" and tok[9] == "->", line
+            mat, (o, e, X, k), q, t = tok[1], map(int, tok[2:6]), tok[6], tok[7]
+            seeds = [tuple(int(v) for v in s.split(":")) for s in tok[8].split(",")]
+            cases.append((mat, o, e, X, k, q, t, seeds, tok[10:]))
+    return cases
+
+
+@pytest.mark.parametrize("case", _golden_xd_cases(), ids=lambda c: f"{c[5]}-{c[6]}-{c[7]}")
+def test_xd_hand_worked(case):
+    mat, o, e, X, k, q, t, seeds, want = case
+    ps = synth.from_strings([q, t])
+    codes = O.encode(ps.ascii)
+    pair = np.zeros(1, O.CAND_DTYPE)
+    pair['i'], pair['j'], pair['count'] = 0, 1, len(seeds)
+    pair['qpos'][0] = [s[0] for s in seeds] + [0xFFFF] * (2 - len(seeds))
+    pair['tpos'][0] = [s[1] for s in seeds] + [0xFFFF] * (2 - len(seeds))
+    rec, cells = O.align_pairs(codes, ps.offsets, pair, _golden_matrix(mat), o, e, O.XD, X, k)
+    r = rec[0]
+    got = [int(r[f]) for f in ("score", "qb", "qe", "tb", "te", "ident", "cols", "seed_used", "passes")]
+    assert got == [int(v) for v in want[:9]]
+    if want[9] != "-":
+        assert cells == int(want[9])
+
+
+def test_filtered_mode_keeps_what_the_filter_needs():
+    """Mode 3 (the filter only, Sec. IV-F): a passing pair's record is SW's, a failing
+    pair keeps SW's score and end with the rest 0, and the edges are SW's."""
+    ps = synth.zipf_100k(n=2000).subset(np.arange(150))
+    codes = O.encode(ps.ascii)
+    rp, code, pos = O.kmers(codes, ps.offsets, 6)
+    c = O.candidates(rp, code, pos, 6, 10, MAT, 1)
+    sw, cs = O.align_pairs(codes, ps.offsets, c, MAT, mode=O.SW)
+    fl, cf = O.align_pairs(codes, ps.offsets, c, MAT, mode=O.SW_FILTERED)
+    assert cs == cf
+    ok = sw['passes'] == 1
+    assert 0 < ok.sum() < len(c)
+    assert fl[ok].tobytes() == sw[ok].tobytes()
+    for f in ("score", "qe", "te"):
+        assert (fl[f] == sw[f]).all()
+    for f in ("qb", "tb", "ident", "cols", "passes"):
+        assert (fl[f][~ok] == 0).all()
+    assert O.filter_edges(ps.offsets, c, fl).tobytes() == O.filter_edges(ps.offsets, c, sw).tobytes()

@@ -229,3 +229,36 @@ def test_substitutes_m0_is_exact_and_monotone():
         prev = keys
     exact = O.candidates(rp, code, pos, 4, 0, MAT, 1)
     assert _as_tuples(exact) == _brute_exact([ps.seq(i) for i in range(ps.n)], 4, 1)
+
+
+# ---- hand-worked symmetrization -------------------------------------------------------
+
+def _golden_sym_cases():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "symmetrize_worked.txt")
+    cases = []
+    with open(path) as f:
+        for line in f:
+            tok = line.split("#", 1)[0].split()
+            if tok:
+                assert tok[0] == "sym" and tok[6] == "->", line
+                cases.append((tok[1], int(tok[2]), int(tok[3]), tok[4], tok[5], [int(v) for v in tok[7:]]))
+    return cases
+
+
+def _matrix_acd():
+    m = np.full((24, 24), -4, np.int8)
+    np.fill_diagonal(m, 5)
+    for a, b, v in (("C", "C", 9), ("D", "D", 9), ("A", "C", 4), ("C", "D", 8)):
+        m[A.index(a), A.index(b)] = m[A.index(b), A.index(a)] = v
+    return m
+
+
+@pytest.mark.parametrize("case", _golden_sym_cases(), ids=lambda c: f"{c[3]}-{c[4]}")
+def test_symmetrization_hand_worked(case):
+    mat, k, m, si, sj, want = case
+    assert mat == "acd"
+    ps, codes, (rp, code, pos) = _oracle_rows([si, sj], k)
+    c = O.candidates(rp, code, pos, k, m, _matrix_acd(), 1)
+    assert len(c) == 1 and (c[0]['i'], c[0]['j']) == (0, 1)
+    assert [int(c[0]['count'])] + [int(v) for v in c[0]['qpos']] + [int(v) for v in c[0]['tpos']] == want
