@@ -35,19 +35,19 @@ import synth  # noqa: E402
 METRIC = "edges/s (whole path: k-mers, A.S.A^T candidates, SW alignment, ANI/coverage filter)"
 UNIT = "edges/s"
 OPS_PER_CELL = 11          # integer ops per SW cell: E 3, F 3, H 4, running best 1
-INT_LANES_PER_SM = 128     # 32-bit integer lanes per SM per clock
 HALVES_PER_LANE = 2        # SW pass 1 works on 16-bit halves, two per 32-bit lane op
-N_SM = 152
+HALF_KINDS = ("viaddmax_s16x2", "vimax3_s16x2_relu", "vadd2", "max3_add2")   # 16x2 instructions
+WORD_KINDS = ("iadd", "imax", "lop3", "imad", "prmt")                        # 32-bit instructions
 SW1_DRAM_BYTES_PER_PAIR = 547_332_608 / 1_086_756
 
 WORKLOADS = {
-    "zipf_100k_s25_sw": dict(n=100_000, m=25, mode=0, desc=(
+    "zipf_100k_s25_sw": dict(n=100_000, m=25, mode=3, desc=(
         "100,000 proteins: 10,000 Zipf(1.5, 1-200) families (80%) + 20% singletons, "
         "lengths log-normal(median 300) clipped 50-1000, 30% BLOSUM62 substitutions + 5% indels; "
         "k=6 with 25 substitute k-mers (C = A S A^T, symmetrized), min_shared 1, "
         "SW int32 BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
-    "zipf_20k_s25_sw": dict(n=20_000, m=25, mode=0, desc="20,000 proteins, same recipe (smaller stand-in)"),
-    "zipf_5k_s25_sw": dict(n=5_000, m=25, mode=0, desc="5,000 proteins, same recipe (profiling stand-in)"),
+    "zipf_20k_s25_sw": dict(n=20_000, m=25, mode=3, desc="20,000 proteins, same recipe (smaller stand-in)"),
+    "zipf_5k_s25_sw": dict(n=5_000, m=25, mode=3, desc="5,000 proteins, same recipe (profiling stand-in)"),
     "zipf_1m_xd": dict(n=1_000_000, m=0, mode=1, desc=(
         "1,000,000 proteins: 100,000 Zipf(1.5, 1-200) families (80%) + 20% singletons, lengths log-normal"
         "(median 300) clipped 50-2000, same mutation recipe; k=6 exact k-mers, min_shared 1, x-drop (X = 49) "
@@ -55,7 +55,7 @@ WORKLOADS = {
     "zipf_20k_xd": dict(n=20_000, m=0, mode=1, desc=(
         "20,000 proteins of the 100,000-protein recipe; k=6 exact k-mers, x-drop (X = 49) from both seeds "
         "(profiling stand-in for the x-drop workloads)")),
-    "families_1k_sw": dict(n=1000, m=0, mode=0, desc=(
+    "families_1k_sw": dict(n=1000, m=0, mode=3, desc=(
         "1,000 proteins = 100 families x 10, k=6 exact, SW int32, ANI 30 / cov 70")),
 }
 
@@ -89,6 +89,18 @@ def combine_ranks(my_ms, my_units, world, dist=None, device=None):
     dist.all_reduce(mx, op=dist.ReduceOp.MAX)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(mx[0]), float(t[1])
+
+
+def default_batches(n):
+    return 64 if n >= 500_000 else 8 if n >= 50_000 else 1
+
+
+def config_of(name, ps, batches, world):
+    """The workload description both arms print (the same keys and values)."""
+    return {"workload": WORKLOADS[name]["desc"], "name": name, "sequences": ps.n, "residues": int(ps.ascii.size),
+            "batch": (f"one of {batches} equal-work query-row blocks (rows i against every j > i); "
+                      f"the blocks together are the whole all-vs-all job"),
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"}
 
 
 def make_set(name, seed_offset=0):
@@ -234,7 +246,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": WORKLOADS[name]["desc"], "name": name},
+            "data": "synthetic",
+            "config": config_of(name, ps, args.batches or default_batches(ps.n), max(1, args.gpus)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gcups": cells / secs / 1e9 if secs > 0 else 0.0}
@@ -611,7 +624,7 @@ def run_serve(args):
     line = {"metric": "serving: query batches vs a resident database (queries/s, p50/p99 latency)",
             "value": st["queries_per_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
             "steps": len(reqs), "warmup": 3, "data": "synthetic",
-            "dtype": "int16x2 / int32" if w["mode"] == 0 else "int32",
+            "dtype": "int16x2 / int32" if w["mode"] != 1 else "int32",
             "config": {"workload": f"database: {w['desc']}; exact k-mers (m = 0)", "name": name,
                        "requests": len(reqs), "request_sizes": "log-uniform 1..4096 queries",
                        "arrivals": f"Poisson, {rate:.3f} requests/s (70% of batch capacity)",
@@ -626,6 +639,22 @@ def run_serve(args):
 # ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
+def run_probe(args):
+    """The integer-pipe throughput probe alone: one line of warp-instructions per SM clock
+    per instruction kind (the measured peak of the alignment roofline)."""
+    import torch
+    import paper_2009_14467_gb300 as P
+    ctx = P.Context(0)
+    rates = {k: max(P.probe_int_throughput(ctx, k, iters=args.probe_iters) for _ in range(2))
+             for k in P.pastis.PROBE_KINDS}
+    props = torch.cuda.get_device_properties(0)
+    print(json.dumps({"probe": "integer-pipe throughput", "unit": "warp-instructions per SM clock",
+                      "sms": props.multi_processor_count, "iters": args.probe_iters,
+                      **{k: round(v, 4) for k, v in rates.items()}}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -640,7 +669,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-1 layout (no tuner)")
     ap.add_argument("--tune-pairs", type=int, default=3_000_000, help="candidates the tuner samples")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
-    ap.add_argument("--mode", default="plain", choices=["plain", "prefilter", "serve", "variants"],
+    ap.add_argument("--probe-iters", type=int, default=20000, help="probe mode: loop iterations per kernel")
+    ap.add_argument("--mode", default="plain", choices=["plain", "prefilter", "serve", "variants", "probe"],
                     help="plain: the exact path (the headline); prefilter: learned prefilter vs plain; "
                          "serve: query batches against a resident database; variants: components, CK, NS")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests in the stream")
@@ -667,6 +697,8 @@ def main():
         return run_serve(args)
     if args.mode == "variants":
         return run_variants(args)
+    if args.mode == "probe":
+        return run_probe(args)
 
     import torch
     import torch.distributed as dist
@@ -695,14 +727,18 @@ def main():
         if world > 1:
             dist.barrier()
 
-    batches = args.batches or (64 if ps.n >= 500_000 else 8 if ps.n >= 50_000 else 1)
+    batches = args.batches or default_batches(ps.n)
     blocks = row_blocks(ps.n, batches)
     counter = [0]
 
     def step():
-        rows = blocks[counter[0] % batches]
+        b = counter[0] % batches
         counter[0] += 1
-        return P.run(ctx, ascii_dev, offs_dev, params, cells, rows=rows)
+        if b == 0:
+            # a new pass over the job: S and AS are built again (the row blocks of one
+            # pass share them), so the steps carry their share of that work
+            ctx.forget()
+        return P.run(ctx, ascii_dev, offs_dev, params, cells, rows=blocks[b])
 
     tune = None
     if w["mode"] != 1 and not args.no_autotune:
@@ -724,6 +760,11 @@ def main():
                 "layout": {f"{32 * b + 1}-{32 * b + 32}": int(extra[b]) for b in np.flatnonzero(extra)},
                 "pass1_cycles_saved_on_sample": round(1.0 - chosen / base, 4) if base > 0 else 0.0}
         del codes, A, cands, qi, sample
+
+    # the integer-pipe peak, measured on this GPU (warp-instructions per SM clock of each
+    # instruction kind, the best of two runs): the alignment roofline divides by it
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    probe = {k: max(P.probe_int_throughput(ctx, k) for _ in range(2)) for k in P.PROBE_KINDS}
 
     for _ in range(args.warmup):
         res = step()
@@ -770,15 +811,18 @@ def main():
     h2d = ascii_host.numel() + offs_host.numel() * 8
     d2h = 0
     e2e_edges = 0
-    n_e2e = max(1, min(args.steps, 2))
+    n_e2e = max(1, min(args.steps, 8))
     for k in range(n_e2e):
         flush.fill_(1)
         torch.cuda.synchronize()
         barrier()
+        b = (args.warmup + k) % batches
         t0 = time.perf_counter()
+        if b == 0:
+            ctx.forget()
         a = ascii_host.to(dev, non_blocking=True)
         o = offs_host.to(dev, non_blocking=True)
-        r = P.run(ctx, a, o, params, rows=blocks[(args.warmup + k) % batches])
+        r = P.run(ctx, a, o, params, rows=blocks[b])
         edges_host = r["edges"].to("cpu")
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
@@ -791,35 +835,44 @@ def main():
         dist.all_reduce(e2e_e, op=dist.ReduceOp.SUM)      # every rank's edges
     e2e_value = float(e2e_e.item()) / (float(e2e_t.item()) / 1000.0)
 
-    # roofline of the dominant kernel: SW pass 1 (integer ALU bound)
+    # roofline of the dominant kernel: SW pass 1 (integer-pipe bound).  Peak: the best
+    # measured 16x2 instruction rate (warp-instructions per SM clock, from the probe) x 32
+    # lanes x 2 halves x SMs x the SM clock sampled under load.
     roof = None
     dominant = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    clk_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    half_rate = max(probe[k] for k in HALF_KINDS)
+    word_rate = max(probe[k] for k in WORD_KINDS)
+    probe_line = {"unit": "warp-instructions per SM clock (best of 2 runs, 4 CTAs x 256 threads per SM)",
+                  **{k: round(v, 3) for k, v in probe.items()},
+                  "sw_mix_cells_per_clk_sm": round(probe["sw_mix"] * 32 / 5.0, 2)}
     if "sw_pass1" in prof:
         n_l, ms_l = prof["sw_pass1"]
         per_launch_cells = total_cells / max(1, n_l)
         achieved = per_launch_cells * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
-        sm_max = (clk or {}).get("sm_max_mhz", 2070.0) or 2070.0
-        peak = N_SM * INT_LANES_PER_SM * HALVES_PER_LANE * sm_max * 1e6 / 1e12
+        peak = n_sm * half_rate * 32 * HALVES_PER_LANE * clk_mhz * 1e6 / 1e12
         # DRAM bytes per launch: the ncu capture of this kernel on the 5,000-protein set of
         # the same recipe measured 547.3 MB for 1,086,756 pairs (the per-row-pair maxima
         # written for pass 2, which grow with the pairs), scaled by the launch's pairs
-        traffic = SW1_DRAM_BYTES_PER_PAIR * cands_total / max(1, args.steps) if w["mode"] == 0 else None
+        traffic = SW1_DRAM_BYTES_PER_PAIR * cands_total / max(1, args.steps) if w["mode"] != 1 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": "ncu DRAM bytes of a 5,000-protein launch scaled by pairs",
                 "kernel": "sw_pass1",
-                "peak_note": (f"{N_SM} SMs x {INT_LANES_PER_SM} 32-bit lanes x {HALVES_PER_LANE} 16-bit halves x "
-                              f"{sm_max:.0f} MHz (derived, not measured)"),
-                "ops_per_cell": OPS_PER_CELL}
+                "peak_note": (f"measured: {n_sm} SMs x {half_rate:.3f} warp-instructions/clk/SM (best 16x2 kind "
+                              f"of the probe) x 32 lanes x {HALVES_PER_LANE} halves x {clk_mhz:.0f} MHz"),
+                "ops_per_cell": OPS_PER_CELL,
+                "cells_per_clk_sm": per_launch_cells / (ms_l / n_l / 1000.0) / (n_sm * clk_mhz * 1e6),
+                "recurrence_mix_cells_per_clk_sm": probe_line["sw_mix_cells_per_clk_sm"]}
 
     if "xd_extend" in prof and "sw_pass1" not in prof:
         # x-drop: int32 recurrence with carries, computed live cells
         n_l, ms_l = prof["xd_extend"]
-        sm_max = (clk or {}).get("sm_max_mhz", 2070.0) or 2070.0
         achieved = total_cells / max(1, n_l) * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
-        peak = N_SM * INT_LANES_PER_SM * sm_max * 1e6 / 1e12
+        peak = n_sm * word_rate * 32 * clk_mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "xd_extend",
-                "peak_note": f"{N_SM} SMs x {INT_LANES_PER_SM} 32-bit lanes x {sm_max:.0f} MHz (derived, not measured)",
+                "peak_note": (f"measured: {n_sm} SMs x {word_rate:.3f} warp-instructions/clk/SM (best 32-bit kind "
+                              f"of the probe) x 32 lanes x {clk_mhz:.0f} MHz"),
                 "ops_per_cell": OPS_PER_CELL, "cells": "computed cells of the x-drop extensions"}
     # roofline of the overlap product (HBM bound): algorithmic bytes = 16 per left-operand
     # entry (its code, position and posting-list bounds), 8 per product (the posting
@@ -883,22 +936,19 @@ def main():
     if rank == 0:
         kernel_ms = {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {
-            "metric": METRIC if w["mode"] == 0 else METRIC.replace("SW alignment", "x-drop alignment"),
+            "metric": METRIC if w["mode"] != 1 else METRIC.replace("SW alignment", "x-drop alignment"),
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-            "dtype": "int16x2 (SW pass 1) / int32" if w["mode"] == 0 else "int32",
-            "config": {"workload": w["desc"], "name": name, "sequences": ps.n, "residues": int(ps.ascii.size),
-                       "batch": (f"one of {batches} equal-work query-row blocks (rows i against every j > i); "
-                                 f"the blocks together are the whole all-vs-all job"),
-                       "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"},
+            "dtype": "int16x2 (SW pass 1) / int32" if w["mode"] != 1 else "int32",
+            "config": config_of(name, ps, batches, world),
             "gcups": total_cells / (my_ms / 1000.0) / 1e9,
             "candidate_pairs_per_s": cands_total / (my_ms / 1000.0),
             "candidates_per_step": cands_total // args.steps, "edges_per_step": edges_total // args.steps,
             "cells_per_step": total_cells // args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant,
+            "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant, "int_probe": probe_line,
             "kernel_ms_timed_region": kernel_ms,
             "sw_on_block": sw_block, "autotune": tune,
             "clocks": clk, "cpu_baseline": cpu,

@@ -65,8 +65,9 @@ enum {
     PASTIS_ERR_INTERNAL = 8          /* a device-side consistency check failed             */
 };
 
-/* Alignment modes (Sec. IV-E; PASTIS_SW_SCORE for the NS weight of Sec. VI-B). */
-enum { PASTIS_SW = 0, PASTIS_XD = 1, PASTIS_SW_SCORE = 2 };
+/* Alignment modes (Sec. IV-E; PASTIS_SW_SCORE for the NS weight of Sec. VI-B;
+ * PASTIS_SW_FILTERED for the edges of Sec. IV-F only, see pastis_align_pairs). */
+enum { PASTIS_SW = 0, PASTIS_XD = 1, PASTIS_SW_SCORE = 2, PASTIS_SW_FILTERED = 3 };
 
 /* Parameters of the method (Sec. VI: k = 6, BLOSUM62, gap open 11, extension 1,
  * x-drop 49, common-k-mer threshold; Sec. IV-F: ANI 30%, coverage 70%).          */
@@ -148,6 +149,13 @@ typedef struct pastis_ctx pastis_ctx;
 pastis_status pastis_ctx_create(pastis_ctx **ctx, int device, void *stream);
 pastis_status pastis_ctx_destroy(pastis_ctx *ctx);
 const char *pastis_status_string(pastis_status s);
+/* Kept results.  A product with substitutes keeps the AS matrix it built (Sec. IV-C)
+ * together with a copy of A's rows; a later product whose A has the same rows (compared
+ * on the device, one read of both copies) and the same k, m and matrix reuses it, so the
+ * row blocks of one job build S and AS once.  The last product's candidates are kept for
+ * the two-phase size protocol.  pastis_ctx_forget drops both, so the next call computes
+ * everything again (the workspace stays allocated).                                 */
+pastis_status pastis_ctx_forget(pastis_ctx *ctx);
 /* Bytes of workspace the context holds now. */
 int64_t pastis_ctx_workspace_bytes(const pastis_ctx *ctx);
 /* Kernel launches the context has issued since creation (for accounting). */
@@ -165,6 +173,29 @@ int32_t pastis_ctx_profile_read(pastis_ctx *ctx, char *buf, int32_t len);
  * records written.  Entries past the third are 0.  Synchronises the stream.                 */
 #define PASTIS_STATS 4
 pastis_status pastis_ctx_stats(pastis_ctx *ctx, int64_t *h_out, int32_t n);
+
+/* ---- integer-pipe throughput probe (a measurement of the GPU, not of the method) ----
+ * Runs one instruction kind (or the instruction mix of the Smith-Waterman pass-1
+ * recurrence, PASTIS_PROBE_SW_MIX) in many independent dependency chains on every SM,
+ * blocks_per_sm CTAs of 256 threads per SM, all resident at once, for `iters`
+ * iterations, and stores the measured rate in warp-instructions per SM clock (clock64
+ * inside each CTA; the slowest CTA counts) in *h_warp_inst_per_clk_sm.  The alignment
+ * roofline divides by this measured rate.  UNSUPPORTED when blocks_per_sm CTAs do not
+ * fit on an SM.  Synchronises.                                                       */
+enum {
+    PASTIS_PROBE_VIADDMAX_S16X2 = 0,   /* max(a + b, c) per 16-bit half        */
+    PASTIS_PROBE_VIMAX3_S16X2_RELU = 1,/* max(a, b, c, 0) per 16-bit half      */
+    PASTIS_PROBE_VADD2 = 2,            /* a + b per 16-bit half                */
+    PASTIS_PROBE_PRMT = 3,             /* byte permute                         */
+    PASTIS_PROBE_IMAD = 4,             /* 32-bit multiply-add                  */
+    PASTIS_PROBE_IMAX = 5,             /* 32-bit signed maximum                */
+    PASTIS_PROBE_LOP3 = 6,             /* (a & b) | c                          */
+    PASTIS_PROBE_IADD = 7,             /* 32-bit add                           */
+    PASTIS_PROBE_SW_MIX = 8,           /* the pass-1 recurrence mix            */
+    PASTIS_PROBE_MAX3_ADD2 = 9         /* 16x2 three-way max and 16x2 add, 1:1 */
+};
+pastis_status pastis_probe_int_throughput(pastis_ctx *ctx, int32_t kind, int32_t blocks_per_sm, int32_t iters,
+                                          double *h_warp_inst_per_clk_sm);
 
 /* ---- a1: encode (Sec. V-B) ---------------------------------------------------- */
 
@@ -243,6 +274,11 @@ pastis_status pastis_query_overlap(pastis_ctx *ctx, const pastis_kmat *Q, const 
  *   ties) is kept, otherwise the best score with passes = 0.
  * PASTIS_SW_SCORE: the Smith-Waterman score and end only (what the NS weight needs;
  *   no traceback): score, qe, te as in PASTIS_SW; qb, tb, ident, cols, passes are 0.
+ * PASTIS_SW_FILTERED: what the filter needs (Sec. IV-F).  A pair that passes gets the
+ *   record of PASTIS_SW; a pair that fails gets PASTIS_SW's score, qe and te with qb,
+ *   tb, ident, cols and passes 0.  pastis_filter_edges gives the same edges as after
+ *   PASTIS_SW.  Pairs whose end (or the rectangle that bounds their path) leaves less
+ *   than the coverage bound on the shorter sequence are never traced back.
  * d_offsets has n_seqs+1 entries; a pair naming a sequence outside [0, n_seqs), or
  * (XD) a seed that does not fit its sequence, gives PASTIS_ERR_INVALID_ARG before any
  * alignment runs.  d_cells (optional, device int64) accumulates the DP cells computed
@@ -409,16 +445,17 @@ pastis_status pastis_ns_edges(pastis_ctx *ctx, const int64_t *d_offsets, int32_t
 pastis_status pastis_components(pastis_ctx *ctx, int32_t n_seqs, const pastis_edge *d_edges, int64_t n_edges,
                                 int32_t *d_labels);
 
-/* ---- a10 without allocation ---------------------------------------------------------
- * The paper has no counterpart of this call: it is pastis_filter_edges (same keep rule
- * of Sec. IV-F, same edges of Sec. VI-B, same pair order, bit-identical output) for
- * callers that may not allocate device memory -- a worker whose device memory is all
+/* ---- the filter without allocation ------------------------------------------------
+ * The paper has no counterpart of this call.  It gives exactly what pastis_filter_edges
+ * gives (the same keep rule, the same edges, the same pair order, bit for bit) for
+ * callers that may not allocate device memory: a worker whose device memory is all
  * committed (a serving slot admitted against a fixed memory budget), or one that must
  * not call cudaFree, which waits for the whole device and so stalls other streams.
  * It takes no context (creating one allocates its workspace) and neither calls
  * cudaMalloc/cudaFree nor any library that allocates: its scratch is one fixed device
  * array of PASTIS_FILTER_STATIC_SCRATCH_BYTES inside this library (a kept count and an
- * offset per tile of 1,024 pairs, an error word, the total).
+ * offset per tile of 1,024 pairs, an error word, the total), which every GPU that loads
+ * the library holds until the process exits.
  *
  * stream      a cudaStream_t (NULL: the legacy default stream) of the current device;
  *             every d_* pointer is device memory of that device, owned by the caller.
@@ -432,7 +469,9 @@ pastis_status pastis_components(pastis_ctx *ctx, int32_t n_seqs, const pastis_ed
  * at zero; the call clears its own error word first.
  * Set-up: the first call on each device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current) and keeps it; make that first call
- * before any stream capture begins.  Every call after it does no set-up.
+ * before any stream capture begins.  A lookup that fails returns PASTIS_ERR_CUDA and is
+ * not kept: the next call on that device tries again.  Every call after a successful
+ * lookup does no set-up.
  * Concurrency: all calls on one device share the one scratch array, so calls that
  * overlap in time (from several threads, or on several streams) race and corrupt each
  * other's result; the caller runs them one at a time per device.

@@ -560,7 +560,8 @@ extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qc
     if (!ctx || !params || reps < 1 || n_pairs < 0) return PASTIS_ERR_INVALID_ARG;
     pastis_status s = check_params(params);
     if (s != PASTIS_OK) return s;
-    if (params->mode != PASTIS_SW && params->mode != PASTIS_SW_SCORE) return PASTIS_ERR_UNSUPPORTED;
+    if (params->mode != PASTIS_SW && params->mode != PASTIS_SW_SCORE && params->mode != PASTIS_SW_FILTERED)
+        return PASTIS_ERR_UNSUPPORTED;
     constexpr int NX = PASTIS_SW_MAX_EXTRA + 1;
     const sw_layout saved = ctx->sw_lay;
     int64_t cyc[NX * PASTIS_SW_BINS] = {0};

@@ -146,6 +146,13 @@ extern "C" pastis_status pastis_ctx_destroy(pastis_ctx *ctx) {
     return PASTIS_OK;
 }
 
+extern "C" pastis_status pastis_ctx_forget(pastis_ctx *ctx) {
+    if (!ctx) return PASTIS_ERR_INVALID_ARG;
+    ctx->spg_valid = 0;
+    ctx->as_valid = 0;
+    return PASTIS_OK;
+}
+
 extern "C" int64_t pastis_ctx_workspace_bytes(const pastis_ctx *ctx) {
     if (!ctx) return 0;
     int64_t t = 0;
@@ -178,7 +185,8 @@ pastis_status check_params(const pastis_params *p) {
     if (p->m_subs < 0 || p->m_subs > PASTIS_MAX_M) return PASTIS_ERR_INVALID_ARG;
     if (p->m_subs > ipow24(p->k) - 1) return PASTIS_ERR_INVALID_ARG;
     if (p->min_shared < 1) return PASTIS_ERR_INVALID_ARG;
-    if (p->mode != PASTIS_SW && p->mode != PASTIS_XD && p->mode != PASTIS_SW_SCORE) return PASTIS_ERR_INVALID_ARG;
+    if (p->mode != PASTIS_SW && p->mode != PASTIS_XD && p->mode != PASTIS_SW_SCORE && p->mode != PASTIS_SW_FILTERED)
+        return PASTIS_ERR_INVALID_ARG;
     if (p->xdrop < 0 || p->xdrop > 1000000) return PASTIS_ERR_INVALID_ARG;
     if (p->gap_open < 0 || p->gap_extend < 0 || p->gap_open > 1000 || p->gap_extend > 1000)
         return PASTIS_ERR_INVALID_ARG;

@@ -7,6 +7,7 @@
 // 1,024 consecutive pairs; the scratch holds one count and one offset per tile.
 #include "internal.cuh"
 
+#include <atomic>
 #include <mutex>
 
 namespace {
@@ -145,13 +146,14 @@ k_fs_scatter(const int64_t *offsets, int32_t n_seqs, const pastis_cand *pairs, c
     }
 }
 
-// The scratch address on each device, looked up once per device with that device
-// current.
+// The scratch address on each device, looked up with that device current.  Only a
+// successful lookup is kept: a failed one (say, made while another thread held a
+// global-mode stream capture) returns PASTIS_ERR_CUDA for that call and the next call
+// on the device tries again.
 constexpr int FS_MAX_DEVICES = 64;
 struct fs_device {
-    std::once_flag once;
-    uint32_t *ptr = nullptr;
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    std::atomic<uint32_t *> ptr{nullptr};
 };
 fs_device g_fs_devices[FS_MAX_DEVICES];
 
@@ -160,13 +162,21 @@ pastis_status fs_scratch(uint32_t **out) {
     if (cudaGetDevice(&dev) != cudaSuccess) return PASTIS_ERR_CUDA;
     if (dev < 0 || dev >= FS_MAX_DEVICES) return PASTIS_ERR_UNSUPPORTED;
     fs_device &d = g_fs_devices[dev];
-    std::call_once(d.once, [&d] {
-        void *p = nullptr;
-        d.err = cudaGetSymbolAddress(&p, g_filter_scratch);
-        d.ptr = (uint32_t *)p;
-    });
-    if (d.err != cudaSuccess || d.ptr == nullptr) return PASTIS_ERR_CUDA;
-    *out = d.ptr;
+    uint32_t *p = d.ptr.load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(d.mu);
+        p = d.ptr.load(std::memory_order_relaxed);
+        if (!p) {
+            void *q = nullptr;
+            if (cudaGetSymbolAddress(&q, g_filter_scratch) != cudaSuccess || q == nullptr) {
+                (void)cudaGetLastError();            // leave no sticky error for the caller's next call
+                return PASTIS_ERR_CUDA;
+            }
+            p = (uint32_t *)q;
+            d.ptr.store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
     return PASTIS_OK;
 }
 

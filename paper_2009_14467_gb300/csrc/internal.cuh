@@ -16,7 +16,7 @@ enum ws_slot {
     WS_KMER_TMP,
     WS_SUB_ROOTS, WS_SUB_CODE, WS_SUB_DIST,
     WS_AS_ROWPTR, WS_AS_CODE, WS_AS_POS, WS_AS_COLPTR, WS_AS_COLSEQ, WS_AS_COLPOS,
-    WS_AS_TMP_KEY,
+    WS_AS_TMP_KEY, WS_AS_KEEP,
     WS_SPG_ROWWORK, WS_SPG_ROWOFF, WS_SPG_TMP, WS_SPG_CURSORS, WS_SPG_BIN,
     WS_SPG_RESULT,
     WS_ALN_SCRATCH, WS_ALN_PASS1, WS_ALN_ORDER, WS_ALN_BOUND, WS_ALN_BOFF,
@@ -32,6 +32,18 @@ __host__ __device__ static inline int sw_bin(int m) {
     const int b = (m - 1) / PASTIS_SW_BIN_WIDTH;
     return b < 0 ? 0 : (b >= PASTIS_SW_BINS ? PASTIS_SW_BINS - 1 : b);
 }
+
+// The AS matrix of A under S (Sec. IV-C) in both views, built inside the overlap
+// product; every array lives in the context's workspace.
+struct as_matrix {
+    int64_t nnz;
+    int64_t *row_ptr;
+    uint32_t *row_code;
+    uint16_t *row_pos;
+    uint32_t *col_ptr;   // dense over 24^k codes
+    int32_t *col_seq;
+    uint16_t *col_pos;
+};
 
 // Per-kernel CUDA-event timing (enabled by pastis_ctx_profile).
 struct prof_rec {
@@ -56,6 +68,13 @@ struct pastis_ctx {
     int32_t spg_key_m, spg_key_min, spg_key_k, spg_key_r0, spg_key_r1;
     uint32_t spg_key_mat_hash;
     int spg_valid;
+    // the AS matrix of the last product with substitutes, kept with what it was built
+    // from: k, m, the matrix, and a copy of A's rows (compared on the device)
+    int as_valid;
+    int32_t as_k, as_m, as_n;
+    int64_t as_nnz_a;
+    int8_t as_mat[PASTIS_NSYM * PASTIS_NSYM];
+    as_matrix as_kept;
     // kept result of the last filter
     int64_t filt_n;
     // profiling: pending event pairs and per-name totals

@@ -31,15 +31,6 @@
 
 #include "internal.cuh"
 
-struct as_matrix {
-    int64_t nnz;
-    int64_t *row_ptr;
-    uint32_t *row_code;
-    uint16_t *row_pos;
-    uint32_t *col_ptr;
-    int32_t *col_seq;
-    uint16_t *col_pos;
-};
 pastis_status build_as(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *p, as_matrix *out);
 
 namespace {

@@ -18,6 +18,8 @@
 // smaller start on ties).  AS is expanded from the rows of A and S, radix-sorted by s
 // (stable, so sequences stay ascending), reduced to one entry per (s, i), and sorted
 // again by sequence for its CSR view.
+#include <string.h>
+
 #include "internal.cuh"
 
 namespace {
@@ -244,18 +246,106 @@ extern "C" pastis_status pastis_substitute_kmers(pastis_ctx *ctx, const uint32_t
     return launch_subkmers(ctx, d_roots, n_roots, params->k, params->m_subs, params, d_sub_code, d_sub_dist);
 }
 
-// The AS matrix of A under S, in both views (internal to the overlap product).
-struct as_matrix {
-    int64_t nnz;
+// Sets *flag when a[x] != b[x] for some x < n.
+template <typename T>
+__global__ void k_differs(const T *__restrict__ a, const T *__restrict__ b, int64_t n, uint32_t *flag) {
+    bool d = false;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        d |= a[x] != b[x];
+    if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// Layout of the kept copy of A's rows: the flag word, then row_ptr, row_code, row_pos.
+struct as_keep_view {
+    uint32_t *flag;
     int64_t *row_ptr;
     uint32_t *row_code;
     uint16_t *row_pos;
-    uint32_t *col_ptr;   // dense over 24^k codes
-    int32_t *col_seq;
-    uint16_t *col_pos;
 };
+static size_t as_keep_bytes(int64_t n, int64_t nnz) {
+    return 256 + sizeof(int64_t) * (size_t)(n + 1) + sizeof(uint32_t) * (size_t)nnz + sizeof(uint16_t) * (size_t)nnz + 64;
+}
+static as_keep_view as_keep_layout(void *base, int64_t n, int64_t nnz) {
+    as_keep_view v;
+    char *p = (char *)base;
+    v.flag = (uint32_t *)p;
+    v.row_ptr = (int64_t *)(p + 256);
+    v.row_code = (uint32_t *)(v.row_ptr + n + 1);
+    v.row_pos = (uint16_t *)(v.row_code + nnz);
+    return v;
+}
+
+// True when the kept AS was built from this A (same rows, compared on the device), k,
+// m and matrix.  Synchronises the stream.
+static pastis_status as_kept_matches(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *p, bool *hit) {
+    *hit = false;
+    if (!ctx->as_valid || ctx->as_k != p->k || ctx->as_m != p->m_subs || ctx->as_n != A->n_rows ||
+        ctx->as_nnz_a != A->nnz || memcmp(ctx->as_mat, p->matrix, sizeof(ctx->as_mat)) != 0)
+        return PASTIS_OK;
+    cudaStream_t st = ctx->stream;
+    const as_keep_view v = as_keep_layout(ctx->ws[WS_AS_KEEP], A->n_rows, A->nnz);
+    PASTIS_CUDA_TRY(cudaMemsetAsync(v.flag, 0, sizeof(uint32_t), st));
+    const int blocks = ctx->sm_count * 8;
+    k_differs<int64_t><<<blocks, 256, 0, st>>>(A->row_ptr, v.row_ptr, (int64_t)A->n_rows + 1, v.flag);
+    PASTIS_LAUNCHED(ctx);
+    if (A->nnz > 0) {
+        k_differs<uint32_t><<<blocks, 256, 0, st>>>(A->row_code, v.row_code, A->nnz, v.flag);
+        PASTIS_LAUNCHED(ctx);
+        k_differs<uint16_t><<<blocks, 256, 0, st>>>(A->row_pos, v.row_pos, A->nnz, v.flag);
+        PASTIS_LAUNCHED(ctx);
+    }
+    uint32_t h = 1;
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(&h, v.flag, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PASTIS_CUDA_TRY(cudaStreamSynchronize(st));
+    *hit = h == 0;
+    return PASTIS_OK;
+}
+
+// Keeps a copy of A's rows beside the AS just built, so that a later product over the
+// same A (another row block) reuses it.
+static pastis_status as_keep(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *p, const as_matrix *AS) {
+    void *base;
+    PASTIS_WS(base, ctx, WS_AS_KEEP, as_keep_bytes(A->n_rows, A->nnz));
+    const as_keep_view v = as_keep_layout(base, A->n_rows, A->nnz);
+    cudaStream_t st = ctx->stream;
+    PASTIS_CUDA_TRY(cudaMemcpyAsync(v.row_ptr, A->row_ptr, sizeof(int64_t) * ((size_t)A->n_rows + 1),
+                                    cudaMemcpyDeviceToDevice, st));
+    if (A->nnz > 0) {
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(v.row_code, A->row_code, sizeof(uint32_t) * (size_t)A->nnz,
+                                        cudaMemcpyDeviceToDevice, st));
+        PASTIS_CUDA_TRY(cudaMemcpyAsync(v.row_pos, A->row_pos, sizeof(uint16_t) * (size_t)A->nnz,
+                                        cudaMemcpyDeviceToDevice, st));
+    }
+    ctx->as_k = p->k;
+    ctx->as_m = p->m_subs;
+    ctx->as_n = A->n_rows;
+    ctx->as_nnz_a = A->nnz;
+    memcpy(ctx->as_mat, p->matrix, sizeof(ctx->as_mat));
+    ctx->as_kept = *AS;
+    ctx->as_valid = 1;
+    return PASTIS_OK;
+}
+
+// Builds AS (Sec. IV-C), or reuses the one kept from the last call when A, k, m and the
+// matrix are unchanged: S depends only on the k-mers present and AS only on A and S, so
+// the row blocks of one job share them.
+pastis_status build_as_fresh(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *p, as_matrix *out);
 
 pastis_status build_as(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *p, as_matrix *out) {
+    bool hit = false;
+    pastis_status s = as_kept_matches(ctx, A, p, &hit);
+    if (s != PASTIS_OK) return s;
+    if (hit) {
+        *out = ctx->as_kept;
+        return PASTIS_OK;
+    }
+    ctx->as_valid = 0;
+    s = build_as_fresh(ctx, A, p, out);
+    if (s != PASTIS_OK) return s;
+    return as_keep(ctx, A, p, out);
+}
+
+pastis_status build_as_fresh(pastis_ctx *ctx, const pastis_kmat *A, const pastis_params *p, as_matrix *out) {
     cudaStream_t st = ctx->stream;
     const int k = p->k, m = p->m_subs;
     const int64_t ncodes = ipow24(k);

@@ -59,6 +59,16 @@ struct sw_score_out {                      // pass 1 result per pair
     int32_t big;                           // scores may not fit the pass-1 key
 };
 
+// The filter-only mode (PASTIS_SW_FILTERED): the traced path lies in the rectangle
+// [rect_i, end_i] x [rect_j, end_j] (the whole up-left rectangle before pass 2 narrows
+// it), so its span on the shorter sequence (i on equal lengths) is at most the
+// rectangle's extent there.  An extent below the coverage bound means the pair cannot
+// pass the filter, and its begin and carried statistics are never needed.
+__device__ __forceinline__ bool cannot_cover(const sw_score_out &r, int lq, int lt, int cov) {
+    const int ext = lq <= lt ? r.end_i + 1 - r.rect_i : r.end_j + 1 - r.rect_j;
+    return 100 * ext < cov * min(lq, lt);
+}
+
 // ---------------------------------------------------------------------------------
 // segments: runs of pairs with the same query, at most SEG_MAX long
 // ---------------------------------------------------------------------------------
@@ -455,7 +465,8 @@ __global__ void __launch_bounds__(SW_THREADS, 5) k_sw_bound(const uint8_t *qcode
                                                          const pastis_cand *pairs, int64_t n_pairs,
                                                          const int8_t *gmat, int o, int e, const int16_t *bm_all,
                                                          const int64_t *bm_off, unsigned long long *next_pair,
-                                                         sw_score_out *res, const int64_t *dn, const int *chk) {
+                                                         sw_score_out *res, int cov_cut, const int64_t *dn,
+                                                         const int *chk) {
     if (dn) n_pairs = *dn;
     if (chk && (chk[0] | chk[1])) return;
     __shared__ int s_mat[PASTIS_NSYM * PASTIS_NSYM];
@@ -482,6 +493,10 @@ __global__ void __launch_bounds__(SW_THREADS, 5) k_sw_bound(const uint8_t *qcode
                 bo_l = bm_off[pl];
                 sc_l = r.score; ei_l = r.end_i; ej_l = r.end_j;
                 ok_l = 1;
+                // the filter-only mode: a pair whose end already rules out coverage
+                if (cov_cut >= 0 &&
+                    cannot_cover(r, (int)(qoffsets[c.i + 1] - qo_l), (int)(toffsets[c.j + 1] - to_l), cov_cut))
+                    ok_l = 0;
             }
         }
         for (int u = 0; u < GRAB; ++u) {
@@ -857,7 +872,7 @@ __device__ void carry_group(const uint8_t *__restrict__ q, int m, const uint8_t 
 }
 
 __device__ void finish_record(pastis_aln &rec, int S, int ei, int ej, int qb, int tb, int ident, int M, int lq,
-                              int lt, int ani, int cov) {
+                              int lt, int ani, int cov, int filtered) {
     rec.score = S;
     rec.qb = (uint16_t)qb; rec.qe = (uint16_t)(ei + 1); rec.tb = (uint16_t)tb; rec.te = (uint16_t)(ej + 1);
     rec.ident = (uint16_t)ident;
@@ -865,6 +880,7 @@ __device__ void finish_record(pastis_aln &rec, int S, int ei, int ej, int qb, in
     const int span = lq <= lt ? ei + 1 - qb : ej + 1 - tb;
     const int L = lq <= lt ? lq : lt;
     rec.passes = (rec.cols > 0 && 100 * ident >= ani * (int)rec.cols && 100 * span >= cov * L) ? 1 : 0;
+    if (filtered && !rec.passes) { rec.qb = rec.tb = 0; rec.ident = rec.cols = 0; }
 }
 
 __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, const int64_t *qoffsets,
@@ -872,7 +888,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                                                          const pastis_cand *pairs, int64_t n_pairs,
                                                          const int8_t *gmat, int o, int e, int ani, int cov,
                                                          stripe3_cell *scratch, int sstride, int *next_pair,
-                                                         const sw_score_out *res, int score_only, pastis_aln *out,
+                                                         const sw_score_out *res, int score_only, int filtered,
+                                                         pastis_aln *out,
                                                          int *err, unsigned long long *cells, const int64_t *dn,
                                                          const int *chk) {
     if (dn) n_pairs = *dn;
@@ -902,10 +919,14 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
             g1 = res[pg];
             if (!score_only && !g1.big && g1.score > 0 && g1.end_i + 1 - g1.rect_i <= GROWS) {
                 const pastis_cand c = pairs[pg];
-                gm = g1.end_i + 1 - g1.rect_i;
-                gn = g1.end_j + 1 - g1.rect_j;
-                gq = qcodes + qoffsets[c.i] + g1.rect_i;
-                gt = tcodes + toffsets[c.j] + g1.rect_j;
+                const bool skip = filtered && cannot_cover(g1, (int)(qoffsets[c.i + 1] - qoffsets[c.i]),
+                                                           (int)(toffsets[c.j + 1] - toffsets[c.j]), cov);
+                if (!skip) {                       // a skipped pair's record comes from the loop below
+                    gm = g1.end_i + 1 - g1.rect_i;
+                    gn = g1.end_j + 1 - g1.rect_j;
+                    gq = qcodes + qoffsets[c.i] + g1.rect_i;
+                    gt = tcodes + toffsets[c.j] + g1.rect_j;
+                }
             }
         }
         int gh;
@@ -918,7 +939,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
             pastis_aln rec;
             rec.seed_used = 0; rec.passes = 0; rec.reserved = 0;
             finish_record(rec, g1.score, g1.end_i, g1.end_j, g1.rect_i + (int)(gb >> 16), g1.rect_j + (int)(gb & 0xFFFF),
-                          (int)(gim >> 16), (int)(gim & 0xFFFF), lq, lt, ani, cov);
+                          (int)(gim >> 16), (int)(gim & 0xFFFF), lq, lt, ani, cov, filtered);
             out[pg] = rec;
         }
         // the others, one warp each
@@ -926,11 +947,12 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
             const int64_t p = p0 + k;
             if (p >= n_pairs) break;
             const sw_score_out r1 = res[p];
-            const bool small = !score_only && !r1.big && r1.score > 0 && r1.end_i + 1 - r1.rect_i <= GROWS;
-            if (small) continue;
             const pastis_cand c = pairs[p];
             const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
             const int lq = (int)(qoffsets[c.i + 1] - qo), lt = (int)(toffsets[c.j + 1] - to);
+            const bool skip = filtered && !r1.big && r1.score > 0 && cannot_cover(r1, lq, lt, cov);
+            const bool small = !score_only && !r1.big && r1.score > 0 && r1.end_i + 1 - r1.rect_i <= GROWS;
+            if (small && !skip) continue;
             pastis_aln rec;
             rec.score = 0; rec.qb = rec.qe = rec.tb = rec.te = 0; rec.ident = rec.cols = 0;
             rec.seed_used = 0; rec.passes = 0; rec.reserved = 0;
@@ -942,11 +964,11 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                                          &im);
                     if (h > 0)
                         finish_record(rec, h, bi, bj, (int)(beg >> 16), (int)(beg & 0xFFFF), (int)(im >> 16),
-                                      (int)(im & 0xFFFF), lq, lt, ani, cov);
+                                      (int)(im & 0xFFFF), lq, lt, ani, cov, filtered);
                     if (score_only) { rec.qb = rec.tb = 0; rec.ident = rec.cols = 0; rec.passes = 0; }
                     if (lane == 0) my_cells += (unsigned long long)lq * lt;
                 }
-            } else if (r1.score > 0 && score_only) {
+            } else if (r1.score > 0 && (score_only || skip)) {
                 rec.score = r1.score;                       // score and end only
                 rec.qe = (uint16_t)(r1.end_i + 1);
                 rec.te = (uint16_t)(r1.end_j + 1);
@@ -970,7 +992,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
 #undef PASTIS_CARRY_CASE
                 if (h != r1.score && lane == 0) atomicExch(err, 1);
                 finish_record(rec, r1.score, r1.end_i, r1.end_j, ri + (int)(beg >> 16), rj + (int)(beg & 0xFFFF),
-                              (int)(im >> 16), (int)(im & 0xFFFF), lq, lt, ani, cov);
+                              (int)(im >> 16), (int)(im & 0xFFFF), lq, lt, ani, cov, filtered);
             }
             if (lane == 0) out[p] = rec;
         }
@@ -1063,6 +1085,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     const int score_only = p->mode == PASTIS_SW_SCORE;
+    const int filtered = p->mode == PASTIS_SW_FILTERED;
     int per_sm2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_sw_bound, SW_THREADS, 0);
     if (per_sm2 < 1) per_sm2 = 1;
@@ -1071,7 +1094,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
         k_sw_bound<<<ctx->sm_count * per_sm2, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets,
                                                                    d_pairs, n_pairs, dmat, p->gap_open, p->gap_extend,
                                                                    bm_all, bm_off, (unsigned long long *)(flags + 10),
-                                                                   res, dn, chk);
+                                                                   res, filtered ? p->cov_min_pct : -1, dn, chk);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
     }
@@ -1079,7 +1102,8 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
     k_sw_carry<<<blocks3, SW_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, dmat,
                                                p->gap_open,
                                                p->gap_extend, p->ani_min_pct, p->cov_min_pct,
-                                               (stripe3_cell *)scratch, sstride, flags + 8, res, score_only, d_out, flags,
+                                               (stripe3_cell *)scratch, sstride, flags + 8, res, score_only, filtered,
+                                               d_out, flags,
                                                (unsigned long long *)d_cells, dn, chk);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);

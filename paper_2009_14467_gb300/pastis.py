@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
-SW, XD, SW_SCORE = 0, 1, 2
+SW, XD, SW_SCORE, SW_FILTERED = 0, 1, 2, 3
 SW_BINS, SW_BIN_WIDTH, SW_MAX_EXTRA = 64, 32, 2     # pass-1 layout per query-length bin
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_RESIDUE", 3: "CAPACITY", 4: "OUT_OF_MEMORY",
@@ -97,6 +97,7 @@ def lib():
             sigs = {
                 "pastis_ctx_create": [ctypes.POINTER(P), ctypes.c_int, P],
                 "pastis_ctx_destroy": [P],
+                "pastis_ctx_forget": [P],
                 "pastis_encode": [P, P, i64, P, ctypes.POINTER(i64)],
                 "pastis_kmat_sizes": [i32, i64, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)],
                 "pastis_build_kmers": [P, P, P, i32, i32, ctypes.POINTER(c_kmat), ctypes.POINTER(i64)],
@@ -164,6 +165,11 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().pastis_ctx_launch_count(self.h))
+
+    def forget(self):
+        """pastis_ctx_forget: drop the kept AS matrix and the kept product, so the next
+        call computes them again."""
+        _check("pastis_ctx_forget", lib().pastis_ctx_forget(self.h))
 
     @property
     def workspace_bytes(self) -> int:
@@ -480,6 +486,25 @@ def filter_edges_static(stream: torch.cuda.Stream, offsets: torch.Tensor, pairs:
         ctypes.c_void_p(stream.cuda_stream), _ptr(offsets), offsets.numel() - 1, _ptr(pairs), _ptr(alns), n,
         ctypes.byref(p), _ptr(out), out.shape[0], ctypes.byref(nout)))
     return nout.value
+
+
+PROBE_KINDS = {"viaddmax_s16x2": 0, "vimax3_s16x2_relu": 1, "vadd2": 2, "prmt": 3, "imad": 4, "imax": 5,
+               "lop3": 6, "iadd": 7, "sw_mix": 8, "max3_add2": 9}
+
+
+def probe_int_throughput(ctx: Context, kind: str, blocks_per_sm: int = 4, iters: int = 20000) -> float:
+    """pastis_probe_int_throughput: measured warp-instructions per SM clock of one integer
+    instruction kind (or the pass-1 recurrence mix) over every SM."""
+    L = lib()
+    if not getattr(L, "_probe_sigs", False):
+        L.pastis_probe_int_throughput.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.POINTER(ctypes.c_double)]
+        L.pastis_probe_int_throughput.restype = ctypes.c_int32
+        L._probe_sigs = True
+    out = ctypes.c_double()
+    _check("pastis_probe_int_throughput", L.pastis_probe_int_throughput(ctx.h, PROBE_KINDS[kind], blocks_per_sm,
+                                                                        iters, ctypes.byref(out)))
+    return out.value
 
 
 def to_records(t: torch.Tensor, dtype: np.dtype) -> np.ndarray:

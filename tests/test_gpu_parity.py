@@ -331,3 +331,54 @@ def test_spgemm_row_blocks_concatenate(P, ctx):
     parts = [P.to_records(P.overlap_spgemm(ctx, A, params, rows=(a, b)), P.CAND_DTYPE)
              for a, b in ((0, 37), (37, 37), (37, 250), (250, 400))]
     assert np.concatenate(parts).tobytes() == whole.tobytes()
+
+
+def test_kept_as_reused_only_for_the_same_rows(P, ctx):
+    """The AS matrix kept between row blocks gives the oracle's candidates in every block;
+    A rebuilt in the same buffers with other rows (same size and entry count) is not
+    mistaken for the kept one; pastis_ctx_forget makes the next call rebuild."""
+    ps = synth.zipf_100k(n=2000).subset(np.arange(300))
+    params = P.Params(matrix=MAT, m_subs=10)
+    A = P.build_kmers(ctx, dev(O.encode(ps.ascii)), dev(ps.offsets), 6)
+
+    def oracle_rows(s, a, b):
+        rp, code, pos = O.kmers(O.encode(s.ascii), s.offsets, 6)
+        c = O.candidates(rp, code, pos, 6, params.m_subs, MAT, 1)
+        return c[(c['i'] >= a) & (c['i'] < b)]
+
+    blocks = [(0, 60), (60, 150), (150, 300)]
+    for a, b in blocks:                       # the first call builds AS, the others reuse it
+        got = P.to_records(P.overlap_spgemm(ctx, A, params, rows=(a, b)), P.CAND_DTYPE)
+        assert got.tobytes() == oracle_rows(ps, a, b).tobytes()
+    # the first two sequences swapped: n and nnz(A) unchanged, the rows differ
+    perm = np.arange(ps.n)
+    perm[[0, 1]] = [1, 0]
+    ps2 = ps.subset(perm)
+    P.build_kmers(ctx, dev(O.encode(ps2.ascii)), dev(ps2.offsets), 6, A=A)
+    got = P.to_records(P.overlap_spgemm(ctx, A, params, rows=(0, 60)), P.CAND_DTYPE)
+    assert got.tobytes() == oracle_rows(ps2, 0, 60).tobytes()
+    ctx.forget()
+    again = P.to_records(P.overlap_spgemm(ctx, A, params, rows=(0, 60)), P.CAND_DTYPE)
+    assert again.tobytes() == got.tobytes()
+
+
+
+@pytest.mark.parametrize("which", ["families", "substitutes", "edge_cases"])
+def test_align_filtered_parity(P, ctx, which):
+    """PASTIS_SW_FILTERED against the oracle's mode 3: every field of every record, on
+    family pairs (most pass), substitute-k-mer candidates (mostly random pairs, most cut
+    before the traceback) and the edge-case set; and the same edges as PASTIS_SW."""
+    if which == "families":
+        ps = synth.families_1k()
+        cands = _cands(P, ctx, ps)[1]
+    elif which == "substitutes":
+        ps = synth.zipf_100k(n=2000).subset(np.arange(300))
+        cands = _cands(P, ctx, ps, m=25)[1]
+    else:
+        ps = edge_case_set()
+        cands = _all_pairs(ps.n)
+    got, want, gc, wc = _align_both(P, ctx, ps, cands, P.SW_FILTERED)
+    assert gc == wc
+    _cmp_alns(got, want)
+    sw, _, _, _ = _align_both(P, ctx, ps, cands, P.SW)
+    assert O.filter_edges(ps.offsets, cands, got).tobytes() == O.filter_edges(ps.offsets, cands, sw).tobytes()

@@ -65,6 +65,35 @@ def test_static_filter_equals_filter_on_candidates(env):
         assert g.tobytes() == ref.tobytes()
 
 
+
+def test_static_filter_allocates_nothing_and_matches_oracle(env):
+    """The call's defining property: with the caller's buffers in place, a call leaves
+    the device's free memory unchanged.  And its edges equal the oracle's filter applied
+    to the same alignments."""
+    from oracle import oracle as O
+    P, ctx = env
+    ps = synth.families_1k()
+    params = P.Params(matrix=MAT)
+    a = torch.from_numpy(ps.ascii).cuda()
+    o = torch.from_numpy(ps.offsets).cuda()
+    codes = P.encode(ctx, a)
+    A = P.build_kmers(ctx, codes, o, 6)
+    cands = P.overlap_spgemm(ctx, A, params)
+    alns = P.align_pairs(ctx, codes, o, cands, params)
+    stream = torch.cuda.current_stream()
+    out = torch.zeros((cands.shape[0], P.REC_BYTES), dtype=torch.uint8, device="cuda")
+    P.filter_edges_static(stream, o, cands, alns, params, out)     # first call: set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    n = P.filter_edges_static(stream, o, cands, alns, params, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    want = O.filter_edges(ps.offsets, P.to_records(cands, P.CAND_DTYPE), P.to_records(alns, P.ALN_DTYPE))
+    assert len(want) > 0
+    assert P.to_records(out[:n], P.EDGE_DTYPE).tobytes() == want.tobytes()
+
+
 def _random_records(P, n, n_seqs, seed):
     rng = np.random.default_rng(seed)
     lens = rng.integers(50, 1001, size=n_seqs)
