@@ -9,9 +9,10 @@ the all-vs-all job into --batches parts of equal work, so the steps together cov
 whole job.  Inputs are resident in HBM.  The default workload is the 100,000-protein
 planted-family set with 25 substitute k-mers and exact int32 SW.
 
-Multi-GPU: the all-vs-all of one set is not split here; each rank runs an independent
-set of the same recipe (seed + rank), so per-GPU work is fixed ("weak" scaling) and
-value = edges of all ranks / the slowest rank's time.
+Multi-GPU: the ranks split the row blocks of one job (rank r runs blocks r, r + N, ...);
+each step is one block per rank, so per-GPU work per step is fixed ("weak" scaling) and
+value = edges of all ranks / the slowest rank's time.  No data-path collective: the
+blocks are independent given the replicated set.
 
 `--impl reference` times the CPU oracle (oracle/) on host cores on bounded samples of
 the same workload instead (the project's reference arm; no GPU work).
@@ -91,6 +92,12 @@ def combine_ranks(my_ms, my_units, world, dist=None, device=None):
     return float(mx[0]), float(t[1])
 
 
+def rank_blocks(batches, world, rank):
+    """The row blocks of one job that rank `rank` of `world` runs, in step order: blocks
+    rank, rank + world, ... (every block goes to exactly one rank)."""
+    return [b for b in range(batches) if b % world == rank]
+
+
 def default_batches(n):
     return 64 if n >= 500_000 else 8 if n >= 50_000 else 1
 
@@ -100,7 +107,7 @@ def config_of(name, ps, batches, world):
     return {"workload": WORKLOADS[name]["desc"], "name": name, "sequences": ps.n, "residues": int(ps.ascii.size),
             "batch": (f"one of {batches} equal-work query-row blocks (rows i against every j > i); "
                       f"the blocks together are the whole all-vs-all job"),
-            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"}
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"row blocks of one job split over {world} rank(s), no data-path collective"}
 
 
 def make_set(name, seed_offset=0):
@@ -258,6 +265,103 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 # learned prefilter vs plain
 # ---------------------------------------------------------------------------------
+class PrefilterLeg:
+    """The learned prefilter against the plain path on row blocks of one set: the MLP is
+    trained on pass/fail labels of the exact path over one block, its threshold is
+    calibrated for a recall target on another, and plain and prefiltered runs are timed
+    on further blocks, with edge recall against the exact edges of the same blocks."""
+
+    def __init__(self, P, F, ctx, a, o, params):
+        self.P, self.F, self.ctx, self.a, self.o, self.params = P, F, ctx, a, o, params
+        self.net = None
+        self.thr = None
+
+    def exact(self, rows):
+        P, ctx, a, o, params = self.P, self.ctx, self.a, self.o, self.params
+        codes = P.encode(ctx, a)
+        A = P.build_kmers(ctx, codes, o, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=rows)
+        alns = P.align_pairs(ctx, codes, o, cands, params)
+        return codes, cands, alns
+
+    def train(self, rows, train_pairs, seed=7):
+        import torch
+        F = self.F
+        t0 = time.perf_counter()
+        codes, cands, alns = self.exact(rows)
+        y = F.labels_from(alns)
+        x = F.features(self.ctx, codes, self.o, cands, self.params)
+        n = x.shape[0]
+        g = torch.Generator(device=x.device).manual_seed(seed)
+        take = torch.randperm(n, device=x.device, generator=g)[:min(n, train_pairs)]
+        xt, yt = x[take].contiguous(), y[take].contiguous()
+        del codes, cands, alns, x, y
+        self.net = F.MLP(seed=11)
+        self.hist = F.train(self.ctx, self.net, xt, yt, epochs=3, batch=65536, lr=2e-3, seed=13)
+        self.n_train = int(xt.shape[0])
+        self.train_s = time.perf_counter() - t0
+
+    def calibrate(self, rows, recall):
+        F = self.F
+        codes, cands, alns = self.exact(rows)
+        yc = F.labels_from(alns)
+        zc = F.forward(self.ctx, self.net, F.features(self.ctx, codes, self.o, cands, self.params))
+        self.thr = F.threshold_for_recall(zc, yc, recall)
+
+    def plain(self, rows):
+        return self.P.run(self.ctx, self.a, self.o, self.params, rows=rows)
+
+    def prefiltered(self, rows):
+        P, F, ctx, a, o, params = self.P, self.F, self.ctx, self.a, self.o, self.params
+        codes = P.encode(ctx, a)
+        A = P.build_kmers(ctx, codes, o, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=rows)
+        z = F.forward(ctx, self.net, F.features(ctx, codes, o, cands, params))
+        kept = F.select(ctx, cands, z, self.thr)
+        alns = P.align_pairs(ctx, codes, o, kept, params)
+        edges = P.filter_edges(ctx, o, kept, alns, params)
+        return dict(cands=cands, kept=kept, edges=edges)
+
+    def compare(self, eval_blocks):
+        import torch
+        P = self.P
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.ctx.stream)
+            out = fn()
+            e1.record(self.ctx.stream)
+            torch.cuda.synchronize()
+            return out, e0.elapsed_time(e1) / 1000.0
+
+        for rows in eval_blocks[:1]:          # warm-up of both forms
+            self.plain(rows)
+            self.prefiltered(rows)
+        t_plain = t_pref = 0.0
+        e_plain = e_pref = c_all = c_kept = missing = 0
+        for rows in eval_blocks:
+            rp, tp = timed(lambda: self.plain(rows))
+            rf, tf = timed(lambda: self.prefiltered(rows))
+            t_plain += tp
+            t_pref += tf
+            ep = P.to_records(rp["edges"], P.EDGE_DTYPE)
+            ef = P.to_records(rf["edges"], P.EDGE_DTYPE)
+            e_plain += len(ep)
+            e_pref += len(ef)
+            c_all += rp["cands"].shape[0]
+            c_kept += rf["kept"].shape[0]
+            kp = set(zip(ep["i"].tolist(), ep["j"].tolist()))
+            missing += sum(1 for i, j in zip(ef["i"].tolist(), ef["j"].tolist()) if (i, j) not in kp)
+        v_plain, v_pref = e_plain / t_plain, e_pref / t_pref
+        return {"speedup": v_pref / v_plain, "edge_recall": e_pref / max(e_plain, 1),
+                "edges_per_s_plain": v_plain, "edges_per_s_prefiltered": v_pref, "edges_not_in_exact": missing,
+                "aligned_pair_reduction": 1.0 - c_kept / max(c_all, 1), "candidates": c_all, "kept": c_kept,
+                "threshold": self.thr, "train_pairs": self.n_train, "train_s": round(self.train_s, 2),
+                "train_loss": self.hist}
+
+
 def run_prefilter(args):
     """Trains the MLP on pass/fail labels of the exact path over one row block of the
     100k set, calibrates the threshold for the recall target on a second block, then
@@ -276,108 +380,34 @@ def run_prefilter(args):
     ctx = P.Context(0)
     batches = args.batches or 16
     blocks = row_blocks(ps.n, batches)
-
-    def exact(rows):
-        codes = P.encode(ctx, a)
-        A = P.build_kmers(ctx, codes, o, 6)
-        cands = P.overlap_spgemm(ctx, A, params, rows=rows)
-        alns = P.align_pairs(ctx, codes, o, cands, params)
-        edges = P.filter_edges(ctx, o, cands, alns, params)
-        return codes, cands, alns, edges
-
-    t0 = time.perf_counter()
-    codes, cands, alns, _ = exact(blocks[0])
-    y = F.labels_from(alns)
-    x = F.features(ctx, codes, o, cands, params)
-    n = x.shape[0]
-    g = torch.Generator(device=dev).manual_seed(7)
-    take = torch.randperm(n, device=dev, generator=g)[:min(n, args.train_pairs)]
-    xt, yt = x[take].contiguous(), y[take].contiguous()
-    net = F.MLP(seed=11)
-    hist = F.train(ctx, net, xt, yt, epochs=3, batch=65536, lr=2e-3, seed=13)
-    n_train = int(xt.shape[0])
-    train_s = time.perf_counter() - t0
+    leg = PrefilterLeg(P, F, ctx, a, o, params)
+    leg.train(blocks[0], args.train_pairs)
     src_desc = w["desc"]
     cal_rows, eval_from = blocks[1], 2
     if args.apply:
         # apply the trained network to a fresh set of another workload (e.g. the exact
         # k-mer x-drop pipeline of the 1,000,000-protein recipe, seed + 1)
-        del codes, cands, alns, x, y, xt, yt
         name = args.apply
         w = WORKLOADS[name]
         ps = make_set(name, seed_offset=1)
-        a = torch.from_numpy(ps.ascii).to(dev)
-        o = torch.from_numpy(ps.offsets).to(dev)
-        params = P.Params(matrix=synth.blosum62(), k=6, m_subs=w["m"], mode=w["mode"])
+        leg.a = torch.from_numpy(ps.ascii).to(dev)
+        leg.o = torch.from_numpy(ps.offsets).to(dev)
+        leg.params = P.Params(matrix=synth.blosum62(), k=6, m_subs=w["m"], mode=w["mode"])
         batches = args.batches or (64 if ps.n >= 500_000 else 16)
         blocks = row_blocks(ps.n, batches)
         cal_rows, eval_from = blocks[0], 1
-    # calibration block
-    codes, cands, alns, _ = exact(cal_rows)
-    yc = F.labels_from(alns)
-    zc = F.forward(ctx, net, F.features(ctx, codes, o, cands, params))
-    thr = F.threshold_for_recall(zc, yc, args.calib_recall)
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        out = fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return out, e0.elapsed_time(e1) / 1000.0
-
-    def plain(rows):
-        return P.run(ctx, a, o, params, rows=rows)
-
-    def prefiltered(rows):
-        codes = P.encode(ctx, a)
-        A = P.build_kmers(ctx, codes, o, 6)
-        cands = P.overlap_spgemm(ctx, A, params, rows=rows)
-        z = F.forward(ctx, net, F.features(ctx, codes, o, cands, params))
-        kept = F.select(ctx, cands, z, thr)
-        alns = P.align_pairs(ctx, codes, o, kept, params)
-        edges = P.filter_edges(ctx, o, kept, alns, params)
-        return dict(cands=cands, kept=kept, edges=edges)
-
+    leg.calibrate(cal_rows, args.calib_recall)
     eval_blocks = [blocks[k] for k in range(eval_from, min(batches, eval_from + max(args.steps, 1)))]
-    for rows in eval_blocks[:1]:          # warm-up of both forms
-        plain(rows)
-        prefiltered(rows)
-    t_plain = t_pref = 0.0
-    e_plain = e_pref = c_all = c_kept = 0
-    missing = 0
-    for rows in eval_blocks:
-        rp, tp = timed(lambda: plain(rows))
-        rf, tf = timed(lambda: prefiltered(rows))
-        t_plain += tp
-        t_pref += tf
-        ep = P.to_records(rp["edges"], P.EDGE_DTYPE)
-        ef = P.to_records(rf["edges"], P.EDGE_DTYPE)
-        e_plain += len(ep)
-        e_pref += len(ef)
-        c_all += rp["cands"].shape[0]
-        c_kept += rf["kept"].shape[0]
-        kp = set(zip(ep["i"].tolist(), ep["j"].tolist()))
-        missing += sum(1 for i, j in zip(ef["i"].tolist(), ef["j"].tolist()) if (i, j) not in kp)
-    recall = e_pref / max(e_plain, 1)
-    line_ok = recall >= args.recall
-    v_plain = e_plain / t_plain
-    v_pref = e_pref / t_pref
+    r = leg.compare(eval_blocks)
     line = {"metric": "prefilter speedup vs plain at >= 99.5% edge recall (edges/s ratio)",
-            "value": v_pref / v_plain, "unit": "x", "higher_is_better": True, "n_gpus": 1,
+            "value": r["speedup"], "unit": "x", "higher_is_better": True, "n_gpus": 1,
             "steps": len(eval_blocks), "warmup": 1, "dtype": "bf16 (MLP) / int16x2 + int32 (alignment)", "data": "synthetic",
             "config": {"workload": w["desc"], "name": name, "batch": f"{len(eval_blocks)} of {batches} equal-work row blocks",
-                       "train": (f"{n_train} labelled candidates of block 0 of: {src_desc}, 3 epochs, Adam 2e-3"
+                       "train": (f"{r['train_pairs']} labelled candidates of block 0 of: {src_desc}, 3 epochs, Adam 2e-3"
                                  + (f"; applied to a fresh set (seed + 1) of {name}" if args.apply else "")),
-                       "calibration": f"threshold {thr:.4f} for recall {args.calib_recall} on one block "
+                       "calibration": f"threshold {r['threshold']:.4f} for recall {args.calib_recall} on one block "
                                       f"(target {args.recall} on the evaluation blocks)"},
-            "recall_target_met": None,
-            "edges_per_s_plain": v_plain, "edges_per_s_prefiltered": v_pref, "edge_recall": recall,
-            "edges_not_in_exact": missing, "aligned_pair_reduction": 1.0 - c_kept / max(c_all, 1),
-            "candidates": c_all, "kept": c_kept, "train_s": train_s, "train_loss": hist}
-    line["recall_target_met"] = line_ok
+            "recall_target_met": r["edge_recall"] >= args.recall, **{k: v for k, v in r.items() if k != "speedup"}}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -666,6 +696,7 @@ def main():
     ap.add_argument("--batches", type=int, default=None,
                     help="equal-work query-row blocks the job is split into (default: 8 for 100k sets, else 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-prefilter", action="store_true", help="plain mode: skip the learned-prefilter leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-1 layout (no tuner)")
     ap.add_argument("--tune-pairs", type=int, default=3_000_000, help="candidates the tuner samples")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
@@ -713,7 +744,7 @@ def main():
     dev = torch.device("cuda", local_rank)
     name = args.workload
     w = WORKLOADS[name]
-    ps = make_set(name, seed_offset=rank)
+    ps = make_set(name)                # one job; the ranks split its row blocks
     mat = synth.blosum62()
     params = P.Params(matrix=mat, k=6, m_subs=w["m"], mode=w["mode"])
     ascii_host = torch.from_numpy(ps.ascii).pin_memory()
@@ -728,17 +759,20 @@ def main():
             dist.barrier()
 
     batches = args.batches or default_batches(ps.n)
+    if batches < world:
+        batches = world
     blocks = row_blocks(ps.n, batches)
+    mine = rank_blocks(batches, world, rank)
     counter = [0]
 
     def step():
-        b = counter[0] % batches
+        k = counter[0] % len(mine)
         counter[0] += 1
-        if b == 0:
-            # a new pass over the job: S and AS are built again (the row blocks of one
-            # pass share them), so the steps carry their share of that work
+        if k == 0:
+            # a new pass over this rank's share of the job: S and AS are built again
+            # (the row blocks of one pass share them), so the steps carry their share
             ctx.forget()
-        return P.run(ctx, ascii_dev, offs_dev, params, cells, rows=blocks[b])
+        return P.run(ctx, ascii_dev, offs_dev, params, cells, rows=blocks[mine[k]])
 
     tune = None
     if w["mode"] != 1 and not args.no_autotune:
@@ -816,13 +850,13 @@ def main():
         flush.fill_(1)
         torch.cuda.synchronize()
         barrier()
-        b = (args.warmup + k) % batches
+        kb = (args.warmup + k) % len(mine)
         t0 = time.perf_counter()
-        if b == 0:
+        if kb == 0:
             ctx.forget()
         a = ascii_host.to(dev, non_blocking=True)
         o = offs_host.to(dev, non_blocking=True)
-        r = P.run(ctx, a, o, params, rows=blocks[b])
+        r = P.run(ctx, a, o, params, rows=blocks[mine[kb]])
         edges_host = r["edges"].to("cpu")
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
@@ -912,6 +946,21 @@ def main():
                     "gcups": int(c_sw.item()) / t / 1e9,
                     "sample": "all candidates of row block 0 of the job (a fixed, seeded block of query rows)"}
 
+    pref = None
+    if w["mode"] != 1 and not args.no_prefilter and batches >= 5 and world == 1:
+        # the learned prefilter against the plain path on this set (bounded: trained on
+        # block 0, calibrated on block 1, timed on blocks 2 and 3)
+        from paper_2009_14467_gb300 import prefilter as F
+        del res
+        leg = PrefilterLeg(P, F, ctx, ascii_dev, offs_dev, params)
+        leg.train(blocks[0], args.train_pairs)
+        leg.calibrate(blocks[1], args.calib_recall)
+        pref = leg.compare([blocks[2], blocks[3]])
+        pref.update({"recall_target": args.recall, "recall_target_met": pref["edge_recall"] >= args.recall,
+                     "blocks": "trained on block 0, threshold calibrated on block 1 for recall "
+                               f"{args.calib_recall}, timed on blocks 2 and 3 of the {batches}"})
+        del leg
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(777)
@@ -951,6 +1000,8 @@ def main():
             "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant, "int_probe": probe_line,
             "kernel_ms_timed_region": kernel_ms,
             "sw_on_block": sw_block, "autotune": tune,
+            "prefilter_speedup": pref["speedup"] if pref else None,
+            "edge_recall": pref["edge_recall"] if pref else None, "prefilter": pref,
             "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

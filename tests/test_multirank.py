@@ -1,7 +1,8 @@
-"""Multi-rank logic on CPU ranks (gloo, world size 2): the equal-work row-block partition
-of one set (the shard a rank would take) and the bench's aggregation over ranks.  Each
-rank computes its block with the oracle; the union of the blocks must equal the
-single-rank result, and the aggregate must be the max time and the summed units."""
+"""Multi-rank logic on CPU ranks (gloo, world size 2): the bench's split of one job into
+equal-work row blocks and its assignment of blocks to ranks (bench.rank_blocks), and the
+bench's aggregation over ranks.  Each rank computes its blocks with the oracle; the
+blocks in order must equal the single-rank result, and the aggregate must be the max
+time and the summed units."""
 import os
 import socket
 
@@ -32,18 +33,26 @@ def _rank_main(rank, world, port, out_dir):
     codes = O.encode(ps.ascii)
     rp, code, pos = O.kmers(codes, ps.offsets, 6)
     cands = O.candidates(rp, code, pos, 6, 0, mat, 1)
-    blocks = bench.row_blocks(ps.n, world)
-    i0, i1 = blocks[rank]
-    mine = cands[(cands["i"] >= i0) & (cands["i"] < i1)]
-    alns, _ = O.align_pairs(codes, ps.offsets, mine, mat)
-    edges = O.filter_edges(ps.offsets, mine, alns)
+    # the bench's own split: equal-work row blocks of one job, rank r taking blocks
+    # r, r + world, ... in step order
+    batches = 5
+    blocks = bench.row_blocks(ps.n, batches)
+    parts = []
+    for b in bench.rank_blocks(batches, world, rank):
+        i0, i1 = blocks[b]
+        mine = cands[(cands["i"] >= i0) & (cands["i"] < i1)]
+        alns, _ = O.align_pairs(codes, ps.offsets, mine, mat)
+        parts.append((b, O.filter_edges(ps.offsets, mine, alns)))
+    n_edges = sum(len(e) for _, e in parts)
     gathered = [None] * world
-    dist.all_gather_object(gathered, edges.tobytes())
-    ms, units = bench.combine_ranks(10.0 * (rank + 1), len(edges), world, dist)
+    dist.all_gather_object(gathered, [(b, e.tobytes()) for b, e in parts])
+    ms, units = bench.combine_ranks(10.0 * (rank + 1), n_edges, world, dist)
     if rank == 0:
-        allb = b"".join(gathered)
+        by_block = sorted(x for g in gathered for x in g)
+        assert [b for b, _ in by_block] == list(range(batches))     # every block exactly once
+        allb = b"".join(e for _, e in by_block)
         ref = O.run(ps.ascii, ps.offsets, mat)["edges"].tobytes()
-        sizes = [len(g) for g in gathered]
+        sizes = [len(e) for _, e in by_block]
         with open(os.path.join(out_dir, "result.txt"), "w") as f:
             f.write(f"{int(allb == ref)} {ms} {units} {sum(sizes) // 20} {len(ref) // 20}\n")
     dist.barrier()
@@ -59,6 +68,13 @@ def test_row_blocks_equal_work_and_cover():
         work = [sum(n - 1 - i for i in range(a, c)) for a, c in blocks]
         if n >= 1000:
             assert max(work) - min(work) <= 2 * n   # a boundary moves by at most one row
+
+
+def test_rank_blocks_cover_each_block_once():
+    import bench
+    for batches, world in ((8, 1), (8, 2), (8, 3), (64, 8), (5, 2)):
+        got = sorted(b for r in range(world) for b in bench.rank_blocks(batches, world, r))
+        assert got == list(range(batches))
 
 
 def test_two_gloo_ranks_partition_the_job(tmp_path):
