@@ -299,7 +299,7 @@ pastis_status pastis_align_pairs_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, co
 
 /* ---- batching: the Smith-Waterman tile layout and its tuner -----------------------
  * Pass 1 of PASTIS_SW / PASTIS_SW_SCORE computes a query of m residues in stripes of
- * 32 lanes x LR rows (LR even, 2..16).  By default it takes as few stripes as 16 rows
+ * 32 lanes x LR rows (LR 2..16).  By default it takes as few stripes as 16 rows
  * per lane allow; a layout adds, per query-length bin (bin = (m-1) / 32, the last bin
  * taking every longer query), 0..PASTIS_SW_MAX_EXTRA stripes, which pads fewer rows
  * but sweeps the target more often.  The layout is a speed choice only: every output

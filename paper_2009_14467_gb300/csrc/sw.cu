@@ -120,13 +120,13 @@ __device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b, uint32_t c) {
 struct end_cell { int h, i, j; };
 
 // Rows per lane: as few stripes as 16 rows per lane allow, plus `extra` stripes (the
-// layout the tuner picked for the query's length bin), then the smallest even row count
-// that covers the query in that many stripes.  More stripes pad fewer rows but sweep the
-// target more often; the layout changes no result.
+// layout the tuner picked for the query's length bin), then the smallest row count
+// (at least 2) that covers the query in that many stripes.  More stripes pad fewer rows
+// but sweep the target more often; the layout changes no result.
 __device__ __forceinline__ int rows_per_lane(int m, int extra) {
     const int ns = max(1, (m + 511) / 512) + extra;
     const int per = (m + 32 * ns - 1) / (32 * ns);
-    return min(16, max(2, (per + 1) & ~1));
+    return min(16, max(2, per));
 }
 
 // The profile holds one signed byte per (target residue, query row): score + o, and
@@ -227,21 +227,25 @@ __device__ void score_pair(const uint8_t *__restrict__ prof, int prow8, const ui
                 if (lane == 31 && !last) out_buf[j] = make_uint2(hup, f);
             }
         }
-        // this lane's rows: first maximum per pair, and the row-pair bounds
+        // this lane's rows: first maximum per pair, and the row-pair bounds.  With LR odd
+        // every other lane starts on an odd row, so the pair (2g, 2g+1) may straddle two
+        // lanes: the lane holding row 2g takes row 2g+1's maximum from the next lane.  A
+        // stripe (32 LR rows) starts on an even row, so no pair straddles two stripes.
+        const int nxa = __shfl_down_sync(0xffffffffu, ((int)kA[0] >> 16) + o, 1);
+        const int nxb = __shfl_down_sync(0xffffffffu, ((int)kB[0] >> 16) + o, 1);
 #pragma unroll
-        for (int r = 0; r < LR; r += 2) {
-            const int xa0 = ((int)kA[r] >> 16) + o, xa1 = ((int)kA[r + 1] >> 16) + o;
-            const int xb0 = ((int)kB[r] >> 16) + o, xb1 = ((int)kB[r + 1] >> 16) + o;
+        for (int r = 0; r < LR; ++r) {
+            const int xa0 = ((int)kA[r] >> 16) + o, xb0 = ((int)kB[r] >> 16) + o;
+            const int xa1 = r + 1 < LR ? ((int)kA[(r + 1) % LR] >> 16) + o : nxa;
+            const int xb1 = r + 1 < LR ? ((int)kB[(r + 1) % LR] >> 16) + o : nxb;
             const int i = row0 + r;
             if (i < m) {
-                bmA[i >> 1] = (int16_t)max(xa0, xa1);
-                bmB[i >> 1] = (int16_t)max(xb0, xb1);
+                if ((i & 1) == 0) {
+                    bmA[i >> 1] = (int16_t)max(xa0, xa1);
+                    bmB[i >> 1] = (int16_t)max(xb0, xb1);
+                }
                 if (xa0 > bA) { bA = xa0; iA = i; jA = 65535 - (int)(kA[r] & 0xFFFFu); }
                 if (xb0 > bB) { bB = xb0; iB = i; jB = 65535 - (int)(kB[r] & 0xFFFFu); }
-            }
-            if (i + 1 < m) {
-                if (xa1 > bA) { bA = xa1; iA = i + 1; jA = 65535 - (int)(kA[r + 1] & 0xFFFFu); }
-                if (xb1 > bB) { bB = xb1; iB = i + 1; jB = 65535 - (int)(kB[r + 1] & 0xFFFFu); }
             }
         }
         __syncwarp();
@@ -635,8 +639,10 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
         score_pair<L>(s_prof, prow8, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, one, my, sstride, bma, bmb, &ea, &eb); \
         break;
                 switch (lr) {
-                    PASTIS_SW_CASE(2) PASTIS_SW_CASE(4) PASTIS_SW_CASE(6) PASTIS_SW_CASE(8)
-                    PASTIS_SW_CASE(10) PASTIS_SW_CASE(12) PASTIS_SW_CASE(14)
+                    PASTIS_SW_CASE(2) PASTIS_SW_CASE(3) PASTIS_SW_CASE(4) PASTIS_SW_CASE(5)
+                    PASTIS_SW_CASE(6) PASTIS_SW_CASE(7) PASTIS_SW_CASE(8) PASTIS_SW_CASE(9)
+                    PASTIS_SW_CASE(10) PASTIS_SW_CASE(11) PASTIS_SW_CASE(12) PASTIS_SW_CASE(13)
+                    PASTIS_SW_CASE(14) PASTIS_SW_CASE(15)
                     default:
                         score_pair<16>(s_prof, prow8, tp[ua], nn[ua], tp[ub], nn[ub], m, o, e, one, my, sstride, bma,
                                        bmb, &ea, &eb);
