@@ -38,7 +38,7 @@ UNIT = "edges/s"
 OPS_PER_CELL = 11          # integer ops per SW cell: E 3, F 3, H 4, running best 1
 HALVES_PER_LANE = 2        # SW pass 1 works on 16-bit halves, two per 32-bit lane op
 HALF_KINDS = ("viaddmax_s16x2", "vimax3_s16x2_relu", "vadd2", "max3_add2")   # 16x2 instructions
-WORD_KINDS = ("iadd", "imax", "lop3", "imad", "prmt")                        # 32-bit instructions
+WORD_KINDS = ("iadd", "imax", "imad", "prmt")    # 32-bit kinds (the logic chain folds under the compiler)
 SW1_DRAM_BYTES_PER_PAIR = 547_332_608 / 1_086_756
 
 WORKLOADS = {
@@ -791,7 +791,10 @@ def main():
         chosen = float(sum(cyc[extra[b], b] for b in range(P.pastis.SW_BINS)))
         tune = {"sample_pairs": int(sample.shape[0]), "sample": f"candidates of every {stride}th query of block 0",
                 "setup_s": round(time.perf_counter() - t0, 2), "bins_changed": int((extra > 0).sum()),
-                "layout": {f"{32 * b + 1}-{32 * b + 32}": int(extra[b]) for b in np.flatnonzero(extra)},
+                "layout": {f"{32 * b + 1}-{32 * b + 32}": ("int32 lanes" if extra[b] == P.pastis.SW_INT32
+                                                            else f"+{int(extra[b])} stripes")
+                           for b in np.flatnonzero(extra)},
+                "int32_vs_int16_cycles": round(float(cyc[P.pastis.SW_INT32].sum()) / max(1.0, float(cyc[0].sum())), 3),
                 "pass1_cycles_saved_on_sample": round(1.0 - chosen / base, 4) if base > 0 else 0.0}
         del codes, A, cands, qi, sample
 

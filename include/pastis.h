@@ -189,7 +189,7 @@ enum {
     PASTIS_PROBE_PRMT = 3,             /* byte permute                         */
     PASTIS_PROBE_IMAD = 4,             /* 32-bit multiply-add                  */
     PASTIS_PROBE_IMAX = 5,             /* 32-bit signed maximum                */
-    PASTIS_PROBE_LOP3 = 6,             /* (a & b) | c                          */
+    PASTIS_PROBE_LOP3 = 6,             /* (a & b) | c; the compiler folds steps */
     PASTIS_PROBE_IADD = 7,             /* 32-bit add                           */
     PASTIS_PROBE_SW_MIX = 8,           /* the pass-1 recurrence mix            */
     PASTIS_PROBE_MAX3_ADD2 = 9         /* 16x2 three-way max and 16x2 add, 1:1 */
@@ -299,29 +299,35 @@ pastis_status pastis_align_pairs_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, co
 
 /* ---- batching: the Smith-Waterman tile layout and its tuner -----------------------
  * Pass 1 of PASTIS_SW / PASTIS_SW_SCORE computes a query of m residues in stripes of
- * 32 lanes x LR rows (LR 2..16).  By default it takes as few stripes as 16 rows
- * per lane allow; a layout adds, per query-length bin (bin = (m-1) / 32, the last bin
- * taking every longer query), 0..PASTIS_SW_MAX_EXTRA stripes, which pads fewer rows
- * but sweeps the target more often.  The layout is a speed choice only: every output
- * of every entry point is the same under every layout.                             */
+ * 32 lanes x LR rows (LR 2..16), two pairs per warp in the 16-bit halves of every
+ * register.  By default it takes as few stripes as 16 rows per lane allow; a layout
+ * sets, per query-length bin (bin = (m-1) / 32, the last bin taking every longer
+ * query), either 0..PASTIS_SW_MAX_EXTRA extra stripes, which pad fewer rows but sweep
+ * the target more often, or PASTIS_SW_INT32: the bin's pairs take one pair per warp in
+ * 32-bit lanes (the whole-matrix path that also serves pairs whose scores could
+ * overflow 16 bits).  The layout is a speed choice only: every output of every entry
+ * point is the same under every layout.                                             */
 #define PASTIS_SW_BINS 64
 #define PASTIS_SW_BIN_WIDTH 32
 #define PASTIS_SW_MAX_EXTRA 2
+#define PASTIS_SW_INT32 3
 
 /* Sets the context's layout from h_extra[PASTIS_SW_BINS] (host; NULL = the default,
- * all 0).  A value above PASTIS_SW_MAX_EXTRA gives PASTIS_ERR_INVALID_ARG and leaves
- * the layout unchanged.  pastis_sw_layout_get copies the current one to h_extra.     */
+ * all 0).  A value other than 0..PASTIS_SW_MAX_EXTRA or PASTIS_SW_INT32 gives
+ * PASTIS_ERR_INVALID_ARG and leaves the layout unchanged.  pastis_sw_layout_get copies
+ * the current one to h_extra.                                                        */
 pastis_status pastis_sw_layout_set(pastis_ctx *ctx, const uint8_t *h_extra);
 pastis_status pastis_sw_layout_get(const pastis_ctx *ctx, uint8_t *h_extra);
 
-/* The autotuner: runs pass 1 over the given pairs (the arguments of
- * pastis_align_pairs_qt; a sample of the workload's candidates) once per uniform
- * layout 0..PASTIS_SW_MAX_EXTRA, `reps` times each, with the SM cycles of every
- * query's work summed per length bin; each bin takes the layout with the fewest cycles
- * when it beats the default by at least 2%, else the default.  The chosen layout is
- * set on the context and copied to h_extra (optional, PASTIS_SW_BINS bytes); h_cycles
- * (optional, host, PASTIS_SW_BINS * (PASTIS_SW_MAX_EXTRA + 1) int64, [x * BINS + bin])
- * receives the measured cycles.  params->mode must be PASTIS_SW or PASTIS_SW_SCORE
+/* The autotuner: runs the score-and-end alignment of the given pairs (the arguments
+ * of pastis_align_pairs_qt; a sample of the workload's candidates) once per uniform
+ * layout 0..PASTIS_SW_MAX_EXTRA and PASTIS_SW_INT32, `reps` times each, with the SM
+ * cycles of every query's pass-1 work and of every pair's 32-bit work summed per
+ * length bin; each bin takes the layout with the fewest cycles when it beats the
+ * default by at least 2%, else the default.  The chosen layout is set on the context
+ * and copied to h_extra (optional, PASTIS_SW_BINS bytes); h_cycles (optional, host,
+ * PASTIS_SW_BINS * (PASTIS_SW_MAX_EXTRA + 2) int64, [x * BINS + bin], x = 0..2 the
+ * extra stripes, x = 3 the 32-bit lanes) receives the measured cycles.  params->mode must be PASTIS_SW or PASTIS_SW_SCORE
  * (PASTIS_ERR_UNSUPPORTED otherwise).  Validation and errors as
  * pastis_align_pairs_qt; the layout is unchanged on error.  Synchronises.           */
 pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,

@@ -536,7 +536,7 @@ extern "C" pastis_status pastis_sw_layout_set(pastis_ctx *ctx, const uint8_t *h_
     sw_layout lay;
     for (int b = 0; b < PASTIS_SW_BINS; ++b) {
         const int v = h_extra ? h_extra[b] : 0;
-        if (v > PASTIS_SW_MAX_EXTRA) return PASTIS_ERR_INVALID_ARG;
+        if (v > PASTIS_SW_MAX_EXTRA && v != PASTIS_SW_INT32) return PASTIS_ERR_INVALID_ARG;
         lay.extra[b] = (uint8_t)v;
     }
     ctx->sw_lay = lay;
@@ -549,9 +549,9 @@ extern "C" pastis_status pastis_sw_layout_get(const pastis_ctx *ctx, uint8_t *h_
     return PASTIS_OK;
 }
 
-// Pass 1 under each uniform layout (score mode: pass 1 and the score-only records), the
-// per-bin cycles of each run summed over reps; per bin the fastest layout when it beats
-// the default by 2% or more.
+// The score-and-end alignment under each uniform layout (the extra stripes of pass 1,
+// then 32-bit lanes for every pair), the per-bin cycles of each run summed over reps;
+// per bin the fastest layout when it beats the default by 2% or more.
 extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
                                             int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
                                             int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
@@ -562,7 +562,7 @@ extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qc
     if (s != PASTIS_OK) return s;
     if (params->mode != PASTIS_SW && params->mode != PASTIS_SW_SCORE && params->mode != PASTIS_SW_FILTERED)
         return PASTIS_ERR_UNSUPPORTED;
-    constexpr int NX = PASTIS_SW_MAX_EXTRA + 1;
+    constexpr int NX = PASTIS_SW_MAX_EXTRA + 2;               // 0..MAX_EXTRA, then PASTIS_SW_INT32
     const sw_layout saved = ctx->sw_lay;
     int64_t cyc[NX * PASTIS_SW_BINS] = {0};
     if (n_pairs > 0) {
@@ -575,7 +575,8 @@ extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qc
         ps.mode = PASTIS_SW_SCORE;
         for (int r = 0; r < reps && s == PASTIS_OK; ++r) {
             for (int x = 0; x < NX && s == PASTIS_OK; ++x) {
-                for (int b = 0; b < PASTIS_SW_BINS; ++b) ctx->sw_lay.extra[b] = (uint8_t)x;
+                const uint8_t v = x <= PASTIS_SW_MAX_EXTRA ? (uint8_t)x : (uint8_t)PASTIS_SW_INT32;
+                for (int b = 0; b < PASTIS_SW_BINS; ++b) ctx->sw_lay.extra[b] = v;
                 ctx->d_tune = d_tune + x * PASTIS_SW_BINS;
                 s = align_qt(ctx, d_qcodes, d_qoffsets, n_q, d_tcodes, d_toffsets, n_t, d_pairs, n_pairs, &ps, d_out,
                              nullptr);
@@ -595,7 +596,7 @@ extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qc
                 bx = x;
         // keep the default unless the winner is clearly faster
         if (bx != 0 && (double)cyc[bx * PASTIS_SW_BINS + b] > 0.98 * (double)cyc[b]) bx = 0;
-        best.extra[b] = (uint8_t)bx;
+        best.extra[b] = bx <= PASTIS_SW_MAX_EXTRA ? (uint8_t)bx : (uint8_t)PASTIS_SW_INT32;
     }
     ctx->sw_lay = best;
     if (h_extra)

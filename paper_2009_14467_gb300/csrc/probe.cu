@@ -38,7 +38,7 @@ __device__ __forceinline__ uint32_t op(uint32_t x, uint32_t y, uint32_t z) {
     else if constexpr (K == PASTIS_PROBE_PRMT) return prmt(x, y, z);
     else if constexpr (K == PASTIS_PROBE_IMAD) return mad_lo(x, y, z);
     else if constexpr (K == PASTIS_PROBE_IMAX) return (uint32_t)max((int)x, (int)y);
-    else if constexpr (K == PASTIS_PROBE_LOP3) return (x & y) | z;
+    else if constexpr (K == PASTIS_PROBE_LOP3) return (x & y) | z;   // consecutive steps fold: counts overstate
     else if constexpr (K == PASTIS_PROBE_MAX3_ADD2) return 0u;   // handled by the caller
     else return x + y;                                        // PASTIS_PROBE_IADD
 }

@@ -36,6 +36,10 @@ pastis_status build_as(pastis_ctx *ctx, const pastis_kmat *A, const pastis_param
 namespace {
 
 constexpr int SPG_THREADS = 256;
+constexpr int SPG_THREADS_MAX = 1024;
+// Threads of a row CTA: the largest tables leave room for one or two CTAs per SM, so
+// their CTAs are wider, keeping up to 32 warps per SM on the posting-list gathers.
+static int spg_threads_for(int tsize) { return tsize >= 4096 ? 1024 : (tsize >= 2048 ? 512 : SPG_THREADS); }
 constexpr int CUR_THREADS = 256;
 constexpr uint64_t SEED_NONE = ~0ull;
 constexpr int32_t J_DONE = 0x7FFFFFFF;     // cursor past its posting list
@@ -153,11 +157,47 @@ __device__ void bitonic_sort_pairs(uint32_t *key, uint32_t *val, int n) {
     }
 }
 
+// Exclusive prefix sums of the popcounts of bits[0, nw) into pre[0, nw), by the whole
+// CTA; returns the total.  Each thread takes a contiguous run of words.
+__device__ uint32_t block_popc_scan(const uint32_t *bits, uint32_t *pre, int nw, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int per = (nw + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
+    uint32_t sum = 0;
+    for (int w = w0; w < w1; ++w) sum += __popc(bits[w]);
+    uint32_t incl = sum;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+    for (int q = 0; q < nwarp; ++q) {
+        const uint32_t v = s_warp[q];
+        off += q < warp ? v : 0u;
+        total += v;
+    }
+    uint32_t run = off + incl - sum;
+    for (int w = w0; w < w1; ++w) {
+        pre[w] = run;
+        run += __popc(bits[w]);
+    }
+    __syncthreads();
+    return total;
+}
+
 // One CTA per row (items of one table size).  SUBS: two orientations per entry
 // (fwd = (AS)_i A_j, bwd = A_i (AS)_j).  Shared memory: s0[T], s1[T] (+ b0[T], b1[T]),
-// key[T], cnt[T] (+ cnt_b[T]), then sort scratch key[T], val[T].
+// key[T], cnt[T] (+ cnt_b[T]), then scratch key[T], val[T].
+// The passing entries of a range [a, z) leave in column order.  When the range is at
+// most 32 T columns wide (the scratch holds a bitmap of it and the popcount prefix of
+// its words), each passing column sets its bit, and an entry's place is the number of
+// set bits before it: no sort.  Otherwise the entries are compacted and bitonic-sorted.
+// The bitmap path clears each slot as it writes it, so the next range starts on a clean
+// table; the sort path clears the whole table at the start of the next range.
 template <bool SUBS>
-__global__ void __launch_bounds__(SPG_THREADS) k_spgemm_rows(operand F, operand B, const row_item *items,
+__global__ void __launch_bounds__(SPG_THREADS_MAX) k_spgemm_rows(operand F, operand B, const row_item *items,
                                                              int tsize, int32_t min_shared, int self, int32_t n_cols,
                                                              cursors cur, pastis_cand *tmp_out, int64_t *item_count,
                                                              int *item_error, unsigned long long *stats) {
@@ -183,17 +223,22 @@ __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_rows(operand F, operand 
     int64_t width = ((int64_t)n_cols - jlo + it.pieces - 1) / it.pieces;
     int64_t out_n = 0;
     unsigned long long n_rec = 0;
+    __shared__ uint32_t s_warp[SPG_THREADS_MAX / 32];
     int64_t a = jlo;
     int guard = 0;
+    bool dirty = true;                           // the table holds entries of an earlier range
     while (a < n_cols) {
         const int32_t z = (int32_t)(a + width < (int64_t)n_cols ? a + width : (int64_t)n_cols);
-        for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
-            s_key[x] = -1;
-            s_cnt[x] = 0;
-            s_s0[x] = SEED_NONE;
-            s_s1[x] = SEED_NONE;
-            if (SUBS) { s_cntb[x] = 0; s_b0[x] = SEED_NONE; s_b1[x] = SEED_NONE; }
+        if (dirty) {
+            for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
+                s_key[x] = -1;
+                s_cnt[x] = 0;
+                s_s0[x] = SEED_NONE;
+                s_s1[x] = SEED_NONE;
+                if (SUBS) { s_cntb[x] = 0; s_b0[x] = SEED_NONE; s_b1[x] = SEED_NONE; }
+            }
         }
+        dirty = true;
         if (threadIdx.x == 0) { s_overflow = 0; s_nvalid = 0; }
         __syncthreads();
         // every cursor up to z
@@ -254,6 +299,70 @@ __global__ void __launch_bounds__(SPG_THREADS) k_spgemm_rows(operand F, operand 
                 return;
             }
             width = (z - a) / 2;
+            continue;
+        }
+        const int64_t wid = (int64_t)z - a;
+        if (wid <= (int64_t)tsize * 32) {
+            // the bitmap of the passing columns of [a, z), then each entry's rank
+            uint32_t *bits = s_sk, *pre = s_sv;
+            const int nw = (int)((wid + 31) >> 5);
+            for (int x = threadIdx.x; x < nw; x += blockDim.x) bits[x] = 0u;
+            __syncthreads();
+            for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
+                const int32_t j = s_key[x];
+                if (j < 0) continue;
+                uint32_t c = s_cnt[x];
+                if (SUBS && s_cntb[x] > c) c = s_cntb[x];
+                if ((int64_t)c < (int64_t)min_shared) continue;
+                const uint32_t off = (uint32_t)(j - (int32_t)a);
+                atomicOr(&bits[off >> 5], 1u << (off & 31));
+            }
+            __syncthreads();
+            const int nv = (int)block_popc_scan(bits, pre, nw, s_warp);
+            if (out_n + nv > it.out_cap) {   // cannot happen: the capacity is the row's products
+                if (threadIdx.x == 0) { item_error[blockIdx.x] = 1; item_count[blockIdx.x] = 0; }
+                return;
+            }
+            for (int x = threadIdx.x; x < tsize; x += blockDim.x) {
+                const int32_t j = s_key[x];
+                if (j < 0) continue;
+                const uint32_t off = (uint32_t)(j - (int32_t)a);
+                const uint32_t word = bits[off >> 5], bit = 1u << (off & 31);
+                if (word & bit) {
+                    pastis_cand rec;
+                    rec.i = i;
+                    rec.j = j;
+                    const bool use_b = SUBS && (s_cntb[x] > s_cnt[x]);
+                    unsigned long long sd[2];
+                    int64_t rb;
+                    const uint16_t *lpos;
+                    if (use_b) {
+                        rec.count = s_cntb[x]; sd[0] = s_b0[x]; sd[1] = s_b1[x]; rb = rb_b; lpos = B.row_pos;
+                    } else {
+                        rec.count = s_cnt[x]; sd[0] = s_s0[x]; sd[1] = s_s1[x]; rb = rb_f; lpos = F.row_pos;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (sd[q] == SEED_NONE) { rec.qpos[q] = 0xFFFF; rec.tpos[q] = 0xFFFF; continue; }
+                        const int64_t t = (int64_t)(sd[q] >> 16);
+                        rec.qpos[q] = lpos[rb + t];
+                        rec.tpos[q] = (uint16_t)(sd[q] & 0xFFFF);
+                    }
+                    const int r = (int)pre[off >> 5] + __popc(word & (bit - 1u));
+                    tmp_out[it.out_off + out_n + r] = rec;
+                }
+                // clear the slot for the next range
+                s_key[x] = -1;
+                s_cnt[x] = 0;
+                s_s0[x] = SEED_NONE;
+                s_s1[x] = SEED_NONE;
+                if (SUBS) { s_cntb[x] = 0; s_b0[x] = SEED_NONE; s_b1[x] = SEED_NONE; }
+            }
+            out_n += nv;
+            n_rec += (unsigned long long)nv;
+            dirty = false;
+            __syncthreads();
+            a = z;
             continue;
         }
         // compact the passing entries of [a, z), sort them by j, append their records
@@ -509,12 +618,13 @@ static pastis_status overlap_impl(pastis_ctx *ctx, const pastis_kmat *A, const p
             for (int64_t g0 = x0; g0 < x1; g0 += 65535) {
                 const int64_t g1 = std::min<int64_t>(x1, g0 + 65535);
                 prof_begin(ctx, "spgemm_rows");
+                const int nth = spg_threads_for(tsize);
                 if (subs)
-                    k_spgemm_rows<true><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
+                    k_spgemm_rows<true><<<(unsigned)(g1 - g0), nth, shm, st>>>(
                         F, Bop, d_items + g0, tsize, params->min_shared, self ? 1 : 0, n_cols, cur, tmp, d_cnt + g0,
                         d_err + g0, stats);
                 else
-                    k_spgemm_rows<false><<<(unsigned)(g1 - g0), SPG_THREADS, shm, st>>>(
+                    k_spgemm_rows<false><<<(unsigned)(g1 - g0), nth, shm, st>>>(
                         F, Bop, d_items + g0, tsize, params->min_shared, self ? 1 : 0, n_cols, cur, tmp, d_cnt + g0,
                         d_err + g0, stats);
                 PASTIS_LAUNCHED(ctx);

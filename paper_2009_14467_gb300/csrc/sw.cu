@@ -567,7 +567,8 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
         const int64_t qo = qoffsets[qi];
         const int m = (int)(qoffsets[qi + 1] - qo);
         const int bin = sw_bin(m);
-        const int ex = extra[bin];
+        const bool int32_bin = extra[bin] == PASTIS_SW_INT32;    // the bin's pairs in 32-bit lanes
+        const int ex = int32_bin ? 0 : extra[bin];
         int lr = rows_per_lane(m, ex);
         int prow8 = ((m + 32 * lr - 1) / (32 * lr)) * STRIPE_BYTES;     // profile bytes per residue
         if (prow8 > prow_cap && ex) {                                  // the extra stripes do not fit
@@ -624,7 +625,8 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_sw_score(const uint8_t *qcode
                 nn[u] = (int)(toffsets[c.j + 1] - to);
                 tp[u] = tcodes + to;
                 if (m == 0 || nn[u] == 0) st[u] = 0;
-                else if (!packable || prow8 > prow_cap || (int64_t)max_s * (int64_t)min(m, nn[u]) >= SCORE_MAX) st[u] = 1;
+                else if (int32_bin || !packable || prow8 > prow_cap ||
+                         (int64_t)max_s * (int64_t)min(m, nn[u]) >= SCORE_MAX) st[u] = 1;
                 else st[u] = 2;
             }
             end_cell res[2];
@@ -896,7 +898,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                                                          stripe3_cell *scratch, int sstride, int *next_pair,
                                                          const sw_score_out *res, int score_only, int filtered,
                                                          pastis_aln *out,
-                                                         int *err, unsigned long long *cells, const int64_t *dn,
+                                                         int *err, unsigned long long *cells,
+                                                         unsigned long long *tune, const int64_t *dn,
                                                          const int *chk) {
     if (dn) n_pairs = *dn;
     if (chk && (chk[0] | chk[1])) return;
@@ -963,6 +966,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
             rec.score = 0; rec.qb = rec.qe = rec.tb = rec.te = 0; rec.ident = rec.cols = 0;
             rec.seed_used = 0; rec.passes = 0; rec.reserved = 0;
             if (r1.big) {
+                const long long t_big = tune ? clock64() : 0;      // the tuner's cycles of 32-bit work
                 if (lq > 0 && lt > 0) {
                     int h, bi, bj;
                     uint32_t beg, im;
@@ -974,6 +978,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_sw_carry(const uint8_t *qcodes, 
                     if (score_only) { rec.qb = rec.tb = 0; rec.ident = rec.cols = 0; rec.passes = 0; }
                     if (lane == 0) my_cells += (unsigned long long)lq * lt;
                 }
+                if (tune && lane == 0) atomicAdd(&tune[sw_bin(lq)], (unsigned long long)(clock64() - t_big));
             } else if (r1.score > 0 && (score_only || skip)) {
                 rec.score = r1.score;                       // score and end only
                 rec.qe = (uint16_t)(r1.end_i + 1);
@@ -1110,7 +1115,7 @@ pastis_status sw_align(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *
                                                p->gap_extend, p->ani_min_pct, p->cov_min_pct,
                                                (stripe3_cell *)scratch, sstride, flags + 8, res, score_only, filtered,
                                                d_out, flags,
-                                               (unsigned long long *)d_cells, dn, chk);
+                                               (unsigned long long *)d_cells, ctx->d_tune, dn, chk);
     PASTIS_LAUNCHED(ctx);
     prof_end(ctx);
     return PASTIS_OK;

@@ -18,6 +18,7 @@ from . import build as _build
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 SW, XD, SW_SCORE, SW_FILTERED = 0, 1, 2, 3
 SW_BINS, SW_BIN_WIDTH, SW_MAX_EXTRA = 64, 32, 2     # pass-1 layout per query-length bin
+SW_INT32 = 3                                        # a layout value: the bin's pairs in 32-bit lanes
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_RESIDUE", 3: "CAPACITY", 4: "OUT_OF_MEMORY",
           5: "CUDA", 6: "TIMEOUT", 7: "UNSUPPORTED", 8: "INTERNAL"}
@@ -336,12 +337,12 @@ def autotune_sw(ctx: Context, codes: torch.Tensor, offsets: torch.Tensor, pairs:
                 reps: int = 2, tcodes: torch.Tensor = None, toffsets: torch.Tensor = None):
     """pastis_autotune_sw over the given pairs (targets in codes/offsets unless tcodes/
     toffsets are given).  Sets the chosen layout on ctx and returns (layout uint8[64],
-    cycles int64[3, 64])."""
+    cycles int64[4, 64]: rows 0-2 the extra stripes, row 3 the 32-bit lanes)."""
     L = _layout_sigs()
     tcodes = codes if tcodes is None else tcodes
     toffsets = offsets if toffsets is None else toffsets
     extra = np.zeros(SW_BINS, np.uint8)
-    cyc = np.zeros((SW_MAX_EXTRA + 1, SW_BINS), np.int64)
+    cyc = np.zeros((SW_MAX_EXTRA + 2, SW_BINS), np.int64)
     p = params.c()
     _check("pastis_autotune_sw", L.pastis_autotune_sw(ctx.h, _ptr(codes), _ptr(offsets), offsets.numel() - 1,
                                                       _ptr(tcodes), _ptr(toffsets), toffsets.numel() - 1,

@@ -1,6 +1,6 @@
-"""The Smith-Waterman pass-1 layout (extra stripes per query-length bin) and its
-autotuner: every layout gives the same records as the default and the oracle, the tuner
-returns and sets a valid layout, and bad layouts or modes are refused."""
+"""The Smith-Waterman pass-1 layout (extra stripes, or 32-bit lanes, per query-length bin)
+and its autotuner: every layout gives the same records as the default and the oracle, the
+tuner returns and sets a valid layout, and bad layouts or modes are refused."""
 import numpy as np
 import pytest
 import torch
@@ -52,6 +52,8 @@ LAYOUTS = {
     "one": np.ones(64, np.uint8),
     "two": np.full(64, 2, np.uint8),
     "mixed": np.random.default_rng(3).integers(0, 3, size=64).astype(np.uint8),
+    "int32": np.full(64, 3, np.uint8),
+    "mixed_int32": np.random.default_rng(4).integers(0, 4, size=64).astype(np.uint8),
 }
 
 
@@ -84,9 +86,9 @@ def test_autotune_sets_a_valid_layout(env):
     params = P.Params(matrix=MAT)
     ctx.set_sw_layout(None)
     extra, cyc = P.autotune_sw(ctx, dev(codes), dev(ps.offsets), recs(c), params, reps=1)
-    assert extra.shape == (64,) and extra.max() <= P.SW_MAX_EXTRA
+    assert extra.shape == (64,) and set(np.unique(extra).tolist()) <= {0, 1, 2, P.SW_INT32}
     assert np.array_equal(ctx.sw_layout(), extra)
-    assert cyc.shape == (3, 64) and (cyc >= 0).all()
+    assert cyc.shape == (4, 64) and (cyc >= 0).all()
     lens = np.diff(ps.offsets)
     bins = np.minimum(63, (lens[np.unique(c["i"])] - 1) // 32)
     for b in np.unique(bins):
@@ -108,7 +110,7 @@ def test_bad_layouts_and_modes_are_refused(env):
     P, ctx = env
     ctx.set_sw_layout(LAYOUTS["one"])
     bad = np.zeros(64, np.uint8)
-    bad[17] = P.SW_MAX_EXTRA + 1
+    bad[17] = P.SW_INT32 + 1
     with pytest.raises(P.PastisError) as e:
         ctx.set_sw_layout(bad)
     assert e.value.status == 1

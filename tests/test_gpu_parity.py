@@ -382,3 +382,4 @@ def test_align_filtered_parity(P, ctx, which):
     _cmp_alns(got, want)
     sw, _, _, _ = _align_both(P, ctx, ps, cands, P.SW)
     assert O.filter_edges(ps.offsets, cands, got).tobytes() == O.filter_edges(ps.offsets, cands, sw).tobytes()
+

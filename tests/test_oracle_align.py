@@ -298,3 +298,4 @@ def test_filtered_mode_keeps_what_the_filter_needs():
     for f in ("qb", "tb", "ident", "cols", "passes"):
         assert (fl[f][~ok] == 0).all()
     assert O.filter_edges(ps.offsets, c, fl).tobytes() == O.filter_edges(ps.offsets, c, sw).tobytes()
+
