@@ -39,7 +39,7 @@ OPS_PER_CELL = 11          # integer ops per SW cell: E 3, F 3, H 4, running bes
 HALVES_PER_LANE = 2        # SW pass 1 works on 16-bit halves, two per 32-bit lane op
 HALF_KINDS = ("viaddmax_s16x2", "vimax3_s16x2_relu", "vadd2", "max3_add2")   # 16x2 instructions
 WORD_KINDS = ("iadd", "imax", "imad", "prmt")    # 32-bit kinds (the logic chain folds under the compiler)
-SW1_DRAM_BYTES_PER_PAIR = 547_332_608 / 1_086_756
+SW1_DRAM_BYTES_PER_PAIR = 551_791_872 / 1_086_756
 
 WORKLOADS = {
     "zipf_100k_s25_sw": dict(n=100_000, m=25, mode=3, desc=(
@@ -360,6 +360,58 @@ class PrefilterLeg:
                 "aligned_pair_reduction": 1.0 - c_kept / max(c_all, 1), "candidates": c_all, "kept": c_kept,
                 "threshold": self.thr, "train_pairs": self.n_train, "train_s": round(self.train_s, 2),
                 "train_loss": self.hist}
+
+
+def xd_leg(P, dev, word_rate, n_sm, clk_mhz, n_blocks=2):
+    """The 1,000,000-protein exact-k-mer x-drop configuration on a bounded sample: one
+    warm-up row block, then `n_blocks` timed row blocks of its 64 (each the whole path:
+    encode, A, candidates, x-drop alignment from both seeds, filter)."""
+    import torch
+    name = "zipf_1m_xd"
+    w = WORKLOADS[name]
+    t0 = time.perf_counter()
+    ps = make_set(name)
+    gen_s = time.perf_counter() - t0
+    params = P.Params(matrix=synth.blosum62(), k=6, m_subs=w["m"], mode=w["mode"])
+    a = torch.from_numpy(ps.ascii).to(dev)
+    o = torch.from_numpy(ps.offsets).to(dev)
+    ctx = P.Context(dev.index or 0)
+    batches = default_batches(ps.n)
+    blocks = row_blocks(ps.n, batches)
+    cells = torch.zeros(1, dtype=torch.int64, device=dev)
+    P.run(ctx, a, o, params, rows=blocks[0])
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ms = 0.0
+    edges = cands = 0
+    for b in range(1, 1 + n_blocks):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        r = P.run(ctx, a, o, params, cells, rows=blocks[b])
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        edges += r["edges"].shape[0]
+        cands += r["cands"].shape[0]
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_cells = int(cells.item())
+    out = {"workload": w["desc"], "name": name, "sequences": ps.n,
+           "blocks": f"row blocks 1-{n_blocks} of {batches} (block 0 as warm-up)",
+           "edges_per_s": edges / (ms / 1000.0), "candidate_pairs_per_s": cands / (ms / 1000.0),
+           "gcups": total_cells / (ms / 1000.0) / 1e9, "ms_per_block": ms / n_blocks,
+           "candidates_per_block": cands // n_blocks, "edges_per_block": edges // n_blocks,
+           "generation_s": round(gen_s, 1),
+           "kernel_ms": {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]}}
+    if "xd_extend" in prof:
+        n_l, ms_l = prof["xd_extend"]
+        ach = total_cells / max(1, n_l) * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
+        peak = n_sm * word_rate * 32 * clk_mhz * 1e6 / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": "xd_extend", "achieved": ach, "peak": peak, "unit": "Tops/s",
+                           "frac": ach / peak, "ops_per_cell": OPS_PER_CELL,
+                           "peak_note": f"measured: {n_sm} SMs x {word_rate:.3f} warp-instructions/clk/SM x 32 lanes"}
+    ctx.close()
+    return out
 
 
 def run_prefilter(args):
@@ -697,6 +749,7 @@ def main():
                     help="equal-work query-row blocks the job is split into (default: 8 for 100k sets, else 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefilter", action="store_true", help="plain mode: skip the learned-prefilter leg")
+    ap.add_argument("--no-xd-leg", action="store_true", help="plain mode: skip the 1M-protein x-drop leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-1 layout (no tuner)")
     ap.add_argument("--tune-pairs", type=int, default=3_000_000, help="candidates the tuner samples")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
@@ -889,7 +942,7 @@ def main():
         achieved = per_launch_cells * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
         peak = n_sm * half_rate * 32 * HALVES_PER_LANE * clk_mhz * 1e6 / 1e12
         # DRAM bytes per launch: the ncu capture of this kernel on the 5,000-protein set of
-        # the same recipe measured 547.3 MB for 1,086,756 pairs (the per-row-pair maxima
+        # the same recipe measured 551.8 MB for 1,086,756 pairs (the per-row-pair maxima
         # written for pass 2, which grow with the pairs), scaled by the launch's pairs
         traffic = SW1_DRAM_BYTES_PER_PAIR * cands_total / max(1, args.steps) if w["mode"] != 1 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
@@ -964,6 +1017,11 @@ def main():
                                f"{args.calib_recall}, timed on blocks 2 and 3 of the {batches}"})
         del leg
 
+    xd = None
+    if w["mode"] != 1 and not args.no_xd_leg and world == 1:
+        # the 1,000,000-protein x-drop configuration, bounded to three row blocks
+        xd = xd_leg(P, dev, word_rate, n_sm, clk_mhz)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(777)
@@ -1003,6 +1061,7 @@ def main():
             "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant, "int_probe": probe_line,
             "kernel_ms_timed_region": kernel_ms,
             "sw_on_block": sw_block, "autotune": tune,
+            "xdrop_1m": xd,
             "prefilter_speedup": pref["speedup"] if pref else None,
             "edge_recall": pref["edge_recall"] if pref else None, "prefilter": pref,
             "clocks": clk, "cpu_baseline": cpu,

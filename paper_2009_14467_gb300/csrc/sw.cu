@@ -165,6 +165,63 @@ __device__ __forceinline__ void column2(const uint8_t *__restrict__ pa, const ui
     }
 }
 
+// The registers a pass-1 stripe sweep carries from column to column, and the values
+// that stay fixed over the sweep.
+template <int LR>
+struct pass1_state {
+    uint32_t (&Ho)[LR], (&E)[LR], (&kA)[LR], (&kB)[LR];
+    uint32_t &hd, &out_h, &out_f, &out_t, &twin, &tnext;
+};
+struct pass1_consts {
+    const uint8_t *pr;
+    int prow8;
+    const uint8_t *tA;
+    int nA;
+    const uint8_t *tB;
+    int nB, n, lane;
+    bool first_stripe, hand_on;
+    uint32_t INIT, sh16, OP, nEP;
+    const uint2 *in_buf;
+    uint2 *out_buf;
+};
+
+// The target window at step s (a multiple of 32): columns [s, s + 32) move to twin,
+// and lane k loads column s + 32 + k of both targets into tnext.
+template <int LR>
+__device__ __forceinline__ void pass1_window(const int s, const pass1_consts &c, pass1_state<LR> &st) {
+    st.twin = st.tnext;
+    const int x = s + 32 + c.lane;
+    st.tnext = (x < c.nA ? (uint32_t)c.tA[x] : (uint32_t)PAD_RES) |
+               ((x < c.nB ? (uint32_t)c.tB[x] : (uint32_t)PAD_RES) << 16);
+}
+
+// One step s of the wavefront: lane l computes column j = s - l of its rows.  CHECKED
+// tests that j is a column (the ramps); `window` = false when the caller loads the
+// target windows itself.
+template <int LR, bool CHECKED>
+__device__ __forceinline__ void pass1_step(const int s, const pass1_consts &c, pass1_state<LR> &st,
+                                           const bool window = true) {
+    const int lane = c.lane, j = s - lane;
+    if (window && s > 0 && (s & 31) == 0) pass1_window<LR>(s, c, st);
+    const uint32_t tw = __shfl_sync(0xffffffffu, st.twin, s & 31);
+    uint32_t hu = __shfl_up_sync(0xffffffffu, st.out_h, 1);
+    uint32_t fu = __shfl_up_sync(0xffffffffu, st.out_f, 1);
+    uint32_t tt = __shfl_up_sync(0xffffffffu, st.out_t, 1);
+    if (lane == 0) {
+        tt = tw;
+        if (c.first_stripe) { hu = c.INIT; fu = c.INIT; }
+        else if (!CHECKED || j < c.n) { const uint2 v = c.in_buf[j]; hu = v.x; fu = v.y; }
+    }
+    if (!CHECKED || (j >= 0 && j < c.n)) {
+        uint32_t f = fu, hup = hu;
+        column2<LR>(c.pr + (int)(tt & 0xFFFFu) * c.prow8, c.pr + (int)(tt >> 16) * c.prow8, st.Ho, st.E, st.kA,
+                    st.kB, st.hd, f, hup, 65535u - (uint32_t)j, c.sh16, c.OP, c.nEP);
+        st.hd = hu;
+        st.out_h = hup; st.out_f = f; st.out_t = tt;
+        if (lane == 31 && c.hand_on) c.out_buf[j] = make_uint2(hup, f);
+    }
+}
+
 // Pass 1 over the whole matrix of two pairs with the same query: pair A (target tA,
 // nA columns) in the low halves, pair B in the high halves.  Lane l owns LR
 // consecutive query rows and at step s does column j = s - l, taking the row above from
@@ -202,31 +259,23 @@ __device__ void score_pair(const uint8_t *__restrict__ prof, int prow8, const ui
                         ((lane < nB ? (uint32_t)tB[lane] : (uint32_t)PAD_RES) << 16);
         uint32_t tnext = (32 + lane < nA ? (uint32_t)tA[32 + lane] : (uint32_t)PAD_RES) |
                          ((32 + lane < nB ? (uint32_t)tB[32 + lane] : (uint32_t)PAD_RES) << 16);
-        for (int s = 0; s < n + 31; ++s) {
-            const int j = s - lane;
-            if (s > 0 && (s & 31) == 0) {
-                twin = tnext;
-                const int c = s + 32 + lane;
-                tnext = (c < nA ? (uint32_t)tA[c] : (uint32_t)PAD_RES) | ((c < nB ? (uint32_t)tB[c] : (uint32_t)PAD_RES) << 16);
-            }
-            const uint32_t tw = __shfl_sync(0xffffffffu, twin, s & 31);
-            uint32_t hu = __shfl_up_sync(0xffffffffu, out_h, 1);
-            uint32_t fu = __shfl_up_sync(0xffffffffu, out_f, 1);
-            uint32_t tt = __shfl_up_sync(0xffffffffu, out_t, 1);
-            if (lane == 0) {
-                tt = tw;
-                if (stripe == 0) { hu = INIT; fu = INIT; }
-                else if (j < n) { const uint2 c = in_buf[j]; hu = c.x; fu = c.y; }
-            }
-            if (j >= 0 && j < n) {
-                uint32_t f = fu, hup = hu;
-                column2<LR>(pr + (int)(tt & 0xFFFFu) * prow8, pr + (int)(tt >> 16) * prow8, Ho, E, kA, kB, hd, f,
-                            hup, 65535u - (uint32_t)j, sh16, OP, nEP);
-                hd = hu;
-                out_h = hup; out_f = f; out_t = tt;
-                if (lane == 31 && !last) out_buf[j] = make_uint2(hup, f);
-            }
+        // Steps [0, 31) and [n, n + 31) are the wavefront's ramps, where some lanes have
+        // no column; in [31, n) every lane has one, so those steps skip the range tests
+        // and run in runs that end at the next 32-column window boundary, the window
+        // loaded once per run instead of tested at every step (measured on the 100k
+        // step: pass 1 -7% against one loop with the tests in every step).
+        pass1_state<LR> st{Ho, E, kA, kB, hd, out_h, out_f, out_t, twin, tnext};
+        const pass1_consts pc{pr, prow8, tA, nA, tB, nB, n, lane, stripe == 0, !last, INIT, sh16, OP, nEP,
+                              in_buf, out_buf};
+        int s = 0;
+        for (const int s_up = min(31, n + 31); s < s_up; ++s) pass1_step<LR, true>(s, pc, st);
+        while (s < n) {
+            if ((s & 31) == 0) pass1_window<LR>(s, pc, st);
+            const int ce = min(n, (s | 31) + 1);          // up to the next window boundary
+#pragma unroll 2
+            for (; s < ce; ++s) pass1_step<LR, false>(s, pc, st, false);
         }
+        for (; s < n + 31; ++s) pass1_step<LR, true>(s, pc, st);
         // this lane's rows: first maximum per pair, and the row-pair bounds.  With LR odd
         // every other lane starts on an odd row, so the pair (2g, 2g+1) may straddle two
         // lanes: the lane holding row 2g takes row 2g+1's maximum from the next lane.  A
