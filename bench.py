@@ -49,11 +49,11 @@ WORKLOADS = {
         "SW int32 BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
     "zipf_20k_s25_sw": dict(n=20_000, m=25, mode=3, desc="20,000 proteins, same recipe (smaller stand-in)"),
     "zipf_5k_s25_sw": dict(n=5_000, m=25, mode=3, desc="5,000 proteins, same recipe (profiling stand-in)"),
-    "zipf_1m_xd": dict(n=1_000_000, m=0, mode=1, desc=(
+    "zipf_1m_xd": dict(n=1_000_000, m=0, mode=4, desc=(
         "1,000,000 proteins: 100,000 Zipf(1.5, 1-200) families (80%) + 20% singletons, lengths log-normal"
         "(median 300) clipped 50-2000, same mutation recipe; k=6 exact k-mers, min_shared 1, x-drop (X = 49) "
         "from both seeds, BLOSUM62 open 11 / extend 1, ANI >= 30%, coverage >= 70%")),
-    "zipf_20k_xd": dict(n=20_000, m=0, mode=1, desc=(
+    "zipf_20k_xd": dict(n=20_000, m=0, mode=4, desc=(
         "20,000 proteins of the 100,000-protein recipe; k=6 exact k-mers, x-drop (X = 49) from both seeds "
         "(profiling stand-in for the x-drop workloads)")),
     "families_1k_sw": dict(n=1000, m=0, mode=3, desc=(
@@ -706,7 +706,7 @@ def run_serve(args):
     line = {"metric": "serving: query batches vs a resident database (queries/s, p50/p99 latency)",
             "value": st["queries_per_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
             "steps": len(reqs), "warmup": 3, "data": "synthetic",
-            "dtype": "int16x2 / int32" if w["mode"] != 1 else "int32",
+            "dtype": "int16x2 / int32" if w["mode"] not in (1, 4) else "int32",
             "config": {"workload": f"database: {w['desc']}; exact k-mers (m = 0)", "name": name,
                        "requests": len(reqs), "request_sizes": "log-uniform 1..4096 queries",
                        "arrivals": f"Poisson, {rate:.3f} requests/s (70% of batch capacity)",
@@ -828,7 +828,7 @@ def main():
         return P.run(ctx, ascii_dev, offs_dev, params, cells, rows=blocks[mine[k]])
 
     tune = None
-    if w["mode"] != 1 and not args.no_autotune:
+    if w["mode"] not in (1, 4) and not args.no_autotune:
         # setup, untimed: the pass-1 layout per query-length bin, tuned on the candidates
         # of every stride-th query of block 0
         t0 = time.perf_counter()
@@ -944,7 +944,7 @@ def main():
         # DRAM bytes per launch: the ncu capture of this kernel on the 5,000-protein set of
         # the same recipe measured 551.8 MB for 1,086,756 pairs (the per-row-pair maxima
         # written for pass 2, which grow with the pairs), scaled by the launch's pairs
-        traffic = SW1_DRAM_BYTES_PER_PAIR * cands_total / max(1, args.steps) if w["mode"] != 1 else None
+        traffic = SW1_DRAM_BYTES_PER_PAIR * cands_total / max(1, args.steps) if w["mode"] not in (1, 4) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": "ncu DRAM bytes of a 5,000-protein launch scaled by pairs",
                 "kernel": "sw_pass1",
@@ -983,7 +983,7 @@ def main():
                     "products": stats["spgemm_products"], "left_entries": stats["spgemm_left_entries"],
                     "records": stats["spgemm_records"]}
     sw_block = None
-    if w["mode"] == 1 and rank == 0:
+    if w["mode"] in (1, 4) and rank == 0:
         # full SW over one block's candidates (the sample of the x-drop workload's pairs)
         sw_params = P.Params(matrix=mat, k=6, m_subs=w["m"], mode=0)
         codes = P.encode(ctx, ascii_dev)
@@ -1003,7 +1003,7 @@ def main():
                     "sample": "all candidates of row block 0 of the job (a fixed, seeded block of query rows)"}
 
     pref = None
-    if w["mode"] != 1 and not args.no_prefilter and batches >= 5 and world == 1:
+    if w["mode"] not in (1, 4) and not args.no_prefilter and batches >= 5 and world == 1:
         # the learned prefilter against the plain path on this set (bounded: trained on
         # block 0, calibrated on block 1, timed on blocks 2 and 3)
         from paper_2009_14467_gb300 import prefilter as F
@@ -1018,7 +1018,7 @@ def main():
         del leg
 
     xd = None
-    if w["mode"] != 1 and not args.no_xd_leg and world == 1:
+    if w["mode"] not in (1, 4) and not args.no_xd_leg and world == 1:
         # the 1,000,000-protein x-drop configuration, bounded to three row blocks
         xd = xd_leg(P, dev, word_rate, n_sm, clk_mhz)
 
@@ -1046,11 +1046,11 @@ def main():
     if rank == 0:
         kernel_ms = {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {
-            "metric": METRIC if w["mode"] != 1 else METRIC.replace("SW alignment", "x-drop alignment"),
+            "metric": METRIC if w["mode"] not in (1, 4) else METRIC.replace("SW alignment", "x-drop alignment"),
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-            "dtype": "int16x2 (SW pass 1) / int32" if w["mode"] != 1 else "int32",
+            "dtype": "int16x2 (SW pass 1) / int32" if w["mode"] not in (1, 4) else "int32",
             "config": config_of(name, ps, batches, world),
             "gcups": total_cells / (my_ms / 1000.0) / 1e9,
             "candidate_pairs_per_s": cands_total / (my_ms / 1000.0),

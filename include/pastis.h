@@ -66,8 +66,9 @@ enum {
 };
 
 /* Alignment modes (Sec. IV-E; PASTIS_SW_SCORE for the NS weight of Sec. VI-B;
- * PASTIS_SW_FILTERED for the edges of Sec. IV-F only, see pastis_align_pairs). */
-enum { PASTIS_SW = 0, PASTIS_XD = 1, PASTIS_SW_SCORE = 2, PASTIS_SW_FILTERED = 3 };
+ * PASTIS_SW_FILTERED and PASTIS_XD_FILTERED for the edges of Sec. IV-F only, see
+ * pastis_align_pairs). */
+enum { PASTIS_SW = 0, PASTIS_XD = 1, PASTIS_SW_SCORE = 2, PASTIS_SW_FILTERED = 3, PASTIS_XD_FILTERED = 4 };
 
 /* Parameters of the method (Sec. VI: k = 6, BLOSUM62, gap open 11, extension 1,
  * x-drop 49, common-k-mer threshold; Sec. IV-F: ANI 30%, coverage 70%).          */
@@ -279,6 +280,11 @@ pastis_status pastis_query_overlap(pastis_ctx *ctx, const pastis_kmat *Q, const 
  *   tb, ident, cols and passes 0.  pastis_filter_edges gives the same edges as after
  *   PASTIS_SW.  Pairs whose end (or the rectangle that bounds their path) leaves less
  *   than the coverage bound on the shorter sequence are never traced back.
+ * PASTIS_XD_FILTERED: the same for x-drop.  A pair that passes gets the record of
+ *   PASTIS_XD; a pair that fails gets PASTIS_XD's score, qe, te and seed_used with qb,
+ *   tb, ident, cols and passes 0.  Every extension is first computed without carried
+ *   statistics; only the seeds whose spans pass the coverage test are extended again
+ *   with them.
  * d_offsets has n_seqs+1 entries; a pair naming a sequence outside [0, n_seqs), or
  * (XD) a seed that does not fit its sequence, gives PASTIS_ERR_INVALID_ARG before any
  * alignment runs.  d_cells (optional, device int64) accumulates the DP cells computed

@@ -25,7 +25,7 @@ EDGE_DTYPE = np.dtype([("i", "<i4"), ("j", "<i4"), ("ident", "<u2"), ("cols", "<
                        ("score", "<i4"), ("weight", "<f4")])
 assert CAND_DTYPE.itemsize == 20 and ALN_DTYPE.itemsize == 20 and EDGE_DTYPE.itemsize == 20
 
-SW, XD, SW_SCORE, SW_FILTERED = 0, 1, 2, 3
+SW, XD, SW_SCORE, SW_FILTERED, XD_FILTERED = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()
 _lib = None

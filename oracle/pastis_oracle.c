@@ -627,8 +627,9 @@ static int passes(const span_stats *s, int32_t lq, int32_t lt, int32_t ani, int3
 /* seeds and keeps the best alignment that passes the filter.  Reading: among   */
 /* passing seeds the higher score wins, the first seed on a tie; when none     */
 /* passes, the best score is reported (first seed on a tie) with passes = 0.    */
-/* Mode 3 is SW for the filter of Sec. IV-F only: a pair that fails keeps its   */
-/* score and end, and its begin, identities and columns are reported as 0.      */
+/* Modes 3 and 4 are SW and XD for the filter of Sec. IV-F only: a pair that    */
+/* fails keeps its score and end (and, for XD, the seed kept), and its begin,   */
+/* identities and columns are reported as 0.                                    */
 int or_align_pairs(const uint8_t *codes, const int64_t *offsets, const or_cand *pairs,
                    int64_t n_pairs, const int8_t *mat, int32_t o, int32_t e, int32_t mode,
                    int32_t X, int32_t k, int32_t ani, int32_t cov, or_aln *out, int64_t *cells) {
@@ -664,6 +665,10 @@ int or_align_pairs(const uint8_t *codes, const int64_t *offsets, const or_cand *
                 else if (pc != ok) take = pc;          /* a passing seed beats a failing one */
                 else take = cur.score > best.score;    /* same status: higher score */
                 if (take) { best = cur; used = s; ok = pc; }
+            }
+            if (mode == 4 && !ok) {
+                best.qb = best.tb = 0;
+                best.ident = best.cols = 0;
             }
         }
         or_aln *r = &out[p];

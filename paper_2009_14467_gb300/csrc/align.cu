@@ -50,6 +50,9 @@ struct xd_bufs {          // per warp, three rotating antidiagonals of (A+2) cel
 };
 
 // qs/ts = +1 for the right extension, -1 for the left one (q[0] is the first residue).
+// CARRY = false computes the same scores, ends and cells without the carried statistics
+// (res->carry = 0): the first phase of the filter-only mode.
+template <bool CARRY>
 __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t, int B, int ts,
                                const int *s_mat, int o, int e, int X, xd_bufs buf, int W, ext_out *res) {
     const int lane = threadIdx.x & 31;
@@ -57,7 +60,7 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
     // antidiagonal 0: the anchor
     if (lane == 0) {
         buf.H[0] = 0; buf.E[0] = NEG; buf.F[0] = NEG;
-        buf.HC[0] = 0; buf.EC[0] = 0; buf.FC[0] = 0;
+        if constexpr (CARRY) { buf.HC[0] = 0; buf.EC[0] = 0; buf.FC[0] = 0; }
     }
     __syncwarp();
     lo[0] = 0; hi[0] = 0;
@@ -87,12 +90,14 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
             uint32_t evc = 0, fvc = 0, dvc = 0;
             if (b >= 1 && a >= lo1 && a <= hi1) {
                 const int eo = H1[a] - o, ex = E1[a] - e;
-                if (eo >= ex) { ev = eo; evc = HC1[a]; } else { ev = ex; evc = EC1[a]; }
+                if (eo >= ex) { ev = eo; if constexpr (CARRY) evc = HC1[a]; }
+                else { ev = ex; if constexpr (CARRY) evc = EC1[a]; }
                 if (ev < NEG) ev = NEG;
             }
             if (a >= 1 && a - 1 >= lo1 && a - 1 <= hi1) {
                 const int fo = H1[a - 1] - o, fx = F1[a - 1] - e;
-                if (fo >= fx) { fv = fo; fvc = HC1[a - 1]; } else { fv = fx; fvc = FC1[a - 1]; }
+                if (fo >= fx) { fv = fo; if constexpr (CARRY) fvc = HC1[a - 1]; }
+                else { fv = fx; if constexpr (CARRY) fvc = FC1[a - 1]; }
                 if (fv < NEG) fv = NEG;
             }
             if (a >= 1 && b >= 1 && a - 1 >= lo2 && a - 1 <= hi2) {
@@ -100,7 +105,7 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
                 if (hd != NEG) {
                     const int qa = q[(long long)(a - 1) * qs], tb = t[(long long)(b - 1) * ts];
                     dv = hd + s_mat[qa * 32 + tb];
-                    dvc = HC2[a - 1] + (qa == tb ? 0x10001u : 1u);
+                    if constexpr (CARRY) dvc = HC2[a - 1] + (qa == tb ? 0x10001u : 1u);
                 }
             }
             int h = dv;
@@ -109,7 +114,7 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
             if (ev > h) { h = ev; hc = evc; }
             if (h < best - X) { h = NEG; ev = NEG; fv = NEG; }
             Hd[a] = h; Ed[a] = ev; Fd[a] = fv;
-            HCd[a] = hc; ECd[a] = evc; FCd[a] = fvc;
+            if constexpr (CARRY) { HCd[a] = hc; ECd[a] = evc; FCd[a] = fvc; }
             if (h != NEG) {
                 my_lo = min(my_lo, a);
                 my_hi = max(my_hi, a);
@@ -123,7 +128,8 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
             my_hi = max(my_hi, __shfl_xor_sync(0xffffffffu, my_hi, x));
             const int ob = __shfl_xor_sync(0xffffffffu, my_best, x);
             const int oa = __shfl_xor_sync(0xffffffffu, my_ba, x);
-            const uint32_t oc = __shfl_xor_sync(0xffffffffu, my_bc, x);
+            uint32_t oc = 0u;
+            if constexpr (CARRY) oc = __shfl_xor_sync(0xffffffffu, my_bc, x);
             if (ob > my_best || (ob == my_best && oa < my_ba)) { my_best = ob; my_ba = oa; my_bc = oc; }
         }
         __syncwarp();
@@ -131,7 +137,7 @@ __device__ void xd_extend_warp(const uint8_t *q, int A, int qs, const uint8_t *t
         if (my_best > best) { best = my_best; ba = my_ba; bb = d - my_ba; bc = my_bc; }
         llo = my_lo; lhi = my_hi;
     }
-    res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
+    res->score = best; res->a = ba; res->b = bb; res->carry = CARRY ? bc : 0u; res->cells = cells;
 }
 
 // The same extension with the cells indexed by diagonal k = a - b instead of by a.  Along
@@ -149,6 +155,7 @@ constexpr int XD_BAND = 64;                 // cells of one antidiagonal: 32 lan
 
 struct xd_src { int h, x; uint32_t hc, xc; };   // a predecessor cell: H, E or F, and carries
 
+template <bool CARRY>
 __device__ __forceinline__ void xd_cell(int a, int b, int d, int clo, int chi, const uint8_t *q, int qs,
                                         const uint8_t *t, int ts, const int *s_mat, int o, int e, int lim,
                                         const xd_src &se, const xd_src &sf, int &H, int &E, int &F, uint32_t &HC,
@@ -158,12 +165,14 @@ __device__ __forceinline__ void xd_cell(int a, int b, int d, int clo, int chi, c
     if (a >= clo && a <= chi) {
         if (b >= 1) {
             const int eo = se.h - o, ex = se.x - e;
-            if (eo >= ex) { ev = eo; evc = se.hc; } else { ev = ex; evc = se.xc; }
+            if (eo >= ex) { ev = eo; if constexpr (CARRY) evc = se.hc; }
+            else { ev = ex; if constexpr (CARRY) evc = se.xc; }
             if (ev < NEG) ev = NEG;
         }
         if (a >= 1) {
             const int fo = sf.h - o, fx = sf.x - e;
-            if (fo >= fx) { fv = fo; fvc = sf.hc; } else { fv = fx; fvc = sf.xc; }
+            if (fo >= fx) { fv = fo; if constexpr (CARRY) fvc = sf.hc; }
+            else { fv = fx; if constexpr (CARRY) fvc = sf.xc; }
             if (fv < NEG) fv = NEG;
         }
         int dv = NEG;
@@ -171,17 +180,18 @@ __device__ __forceinline__ void xd_cell(int a, int b, int d, int clo, int chi, c
         if (a >= 1 && b >= 1 && H != NEG) {
             const int qa = q[(long long)(a - 1) * qs], tb = t[(long long)(b - 1) * ts];
             dv = H + s_mat[qa * 32 + tb];
-            dvc = HC + (qa == tb ? 0x10001u : 1u);
+            if constexpr (CARRY) dvc = HC + (qa == tb ? 0x10001u : 1u);
         }
         h = dv; hc = dvc;
-        if (fv > h) { h = fv; hc = fvc; }
-        if (ev > h) { h = ev; hc = evc; }
+        if (fv > h) { h = fv; if constexpr (CARRY) hc = fvc; }
+        if (ev > h) { h = ev; if constexpr (CARRY) hc = evc; }
         if (h < lim) { h = NEG; ev = NEG; fv = NEG; }
     }
     (void)d;
     H = h; E = ev; F = fv; HC = hc; EC = evc; FC = fvc;
 }
 
+template <bool CARRY>
 __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, int B, int ts, const int *s_mat,
                              int o, int e, int X, ext_out *res) {
     const int lane = threadIdx.x & 31;
@@ -213,11 +223,13 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
             for (int m = 0; m < 4; ++m) {
                 const int h = __shfl_sync(0xffffffffu, H[m], src & 31), ee = __shfl_sync(0xffffffffu, E[m], src & 31);
                 const int ff = __shfl_sync(0xffffffffu, F[m], src & 31);
-                const uint32_t hc = __shfl_sync(0xffffffffu, HC[m], src & 31);
-                const uint32_t ec = __shfl_sync(0xffffffffu, EC[m], src & 31);
-                const uint32_t fc = __shfl_sync(0xffffffffu, FC[m], src & 31);
                 H[m] = in ? h : NEG; E[m] = in ? ee : NEG; F[m] = in ? ff : NEG;
-                HC[m] = in ? hc : 0u; EC[m] = in ? ec : 0u; FC[m] = in ? fc : 0u;
+                if constexpr (CARRY) {
+                    const uint32_t hc = __shfl_sync(0xffffffffu, HC[m], src & 31);
+                    const uint32_t ec = __shfl_sync(0xffffffffu, EC[m], src & 31);
+                    const uint32_t fc = __shfl_sync(0xffffffffu, FC[m], src & 31);
+                    HC[m] = in ? hc : 0u; EC[m] = in ? ec : 0u; FC[m] = in ? fc : 0u;
+                }
             }
         }
         const int lim = best - X;
@@ -228,28 +240,34 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
             // cells on m = 0 and m = 2; F of m = 0 is the previous lane's m = 3
             xd_src up;
             up.h = __shfl_up_sync(0xffffffffu, H[3], 1); up.x = __shfl_up_sync(0xffffffffu, F[3], 1);
-            up.hc = __shfl_up_sync(0xffffffffu, HC[3], 1); up.xc = __shfl_up_sync(0xffffffffu, FC[3], 1);
+            up.hc = 0u; up.xc = 0u;
+            if constexpr (CARRY) {
+                up.hc = __shfl_up_sync(0xffffffffu, HC[3], 1); up.xc = __shfl_up_sync(0xffffffffu, FC[3], 1);
+            }
             if (lane == 0) { up.h = NEG; up.x = NEG; }
             const xd_src e0{H[1], E[1], HC[1], EC[1]}, e2{H[3], E[3], HC[3], EC[3]};
             const xd_src f2{H[1], F[1], HC[1], FC[1]};
             a0 = (d + k0) >> 1;
-            xd_cell(a0, d - a0, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e0, up, H[0], E[0], F[0], HC[0], EC[0],
+            xd_cell<CARRY>(a0, d - a0, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e0, up, H[0], E[0], F[0], HC[0], EC[0],
                     FC[0]);
-            xd_cell(a0 + 1, d - a0 - 1, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e2, f2, H[2], E[2], F[2], HC[2],
+            xd_cell<CARRY>(a0 + 1, d - a0 - 1, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e2, f2, H[2], E[2], F[2], HC[2],
                     EC[2], FC[2]);
             h0 = H[0]; h1 = H[2]; c0 = HC[0]; c1 = HC[2];
         } else {
             // cells on m = 1 and m = 3; E of m = 3 is the next lane's m = 0
             xd_src dn;
             dn.h = __shfl_down_sync(0xffffffffu, H[0], 1); dn.x = __shfl_down_sync(0xffffffffu, E[0], 1);
-            dn.hc = __shfl_down_sync(0xffffffffu, HC[0], 1); dn.xc = __shfl_down_sync(0xffffffffu, EC[0], 1);
+            dn.hc = 0u; dn.xc = 0u;
+            if constexpr (CARRY) {
+                dn.hc = __shfl_down_sync(0xffffffffu, HC[0], 1); dn.xc = __shfl_down_sync(0xffffffffu, EC[0], 1);
+            }
             if (lane == 31) { dn.h = NEG; dn.x = NEG; }
             const xd_src e1{H[2], E[2], HC[2], EC[2]}, f1{H[0], F[0], HC[0], FC[0]};
             const xd_src f3{H[2], F[2], HC[2], FC[2]};
             a0 = (d + k0 + 1) >> 1;
-            xd_cell(a0, d - a0, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e1, f1, H[1], E[1], F[1], HC[1], EC[1],
+            xd_cell<CARRY>(a0, d - a0, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, e1, f1, H[1], E[1], F[1], HC[1], EC[1],
                     FC[1]);
-            xd_cell(a0 + 1, d - a0 - 1, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, dn, f3, H[3], E[3], F[3], HC[3],
+            xd_cell<CARRY>(a0 + 1, d - a0 - 1, d, clo, chi, q, qs, t, ts, s_mat, o, e, lim, dn, f3, H[3], E[3], F[3], HC[3],
                     EC[3], FC[3]);
             h0 = H[1]; h1 = H[3]; c0 = HC[1]; c1 = HC[3];
         }
@@ -265,8 +283,10 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
         const int toph = __reduce_max_sync(0xffffffffu, myh);
         if (toph > best) {
             const int ta = (int)__reduce_min_sync(0xffffffffu, myh == toph ? (unsigned)mya : 0xFFFFFFFFu);
-            const unsigned who = __ballot_sync(0xffffffffu, myh == toph && mya == ta);
-            bc = __shfl_sync(0xffffffffu, myc, __ffs(who) - 1);
+            if constexpr (CARRY) {
+                const unsigned who = __ballot_sync(0xffffffffu, myh == toph && mya == ta);
+                bc = __shfl_sync(0xffffffffu, myc, __ffs(who) - 1);
+            }
             best = toph; ba = ta; bb = d - ta;
         }
         const int first = __ffs(live) - 1, lastl = 31 - __clz(live);
@@ -274,16 +294,20 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
         llo = __shfl_sync(0xffffffffu, lo_here, first);
         lhi = __shfl_sync(0xffffffffu, hi_here, lastl);
     }
-    res->score = best; res->a = ba; res->b = bb; res->carry = bc; res->cells = cells;
+    res->score = best; res->a = ba; res->b = bb; res->carry = CARRY ? bc : 0u; res->cells = cells;
     return true;
 }
 
+// Extension tasks: task = 4 p + 2 seed + left.  With a task list the kernel runs only
+// the listed tasks (*d_ntask of them): the second phase of the filter-only mode.
+template <bool CARRY>
 __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, const int64_t *qoffsets,
                                                         const uint8_t *tcodes, const int64_t *toffsets,
                                                         const pastis_cand *pairs, int64_t n_pairs, int k,
                                                         const int8_t *gmat, int o, int e, int X, int32_t *gbuf,
-                                                        int W, int *next_task, ext_out *out, const int64_t *dn,
-                                                        const int *chk) {
+                                                        int W, int *next_task, ext_out *out,
+                                                        const uint32_t *task_list, const uint32_t *d_ntask,
+                                                        const int64_t *dn, const int *chk) {
     if (dn) n_pairs = *dn;                       // captured launches: count in device memory
     if (chk && (chk[0] | chk[1])) return;        // ... and nothing on bad input
     __shared__ int s_mat[(PASTIS_NSYM + 1) * 32];
@@ -295,12 +319,13 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, c
     int32_t *base = gbuf + (size_t)gw * 18 * W;
     buf.H = base; buf.E = base + 3 * W; buf.F = base + 6 * W;
     buf.HC = (uint32_t *)(base + 9 * W); buf.EC = (uint32_t *)(base + 12 * W); buf.FC = (uint32_t *)(base + 15 * W);
-    const int64_t ntask = n_pairs * 4;
+    const int64_t ntask = task_list ? (int64_t)*d_ntask : n_pairs * 4;
     for (;;) {
-        int64_t task = 0;
-        if (lane == 0) task = atomicAdd((unsigned long long *)next_task, 1ull);
-        task = __shfl_sync(0xffffffffu, task, 0);
-        if (task >= ntask) break;
+        int64_t slot = 0;
+        if (lane == 0) slot = atomicAdd((unsigned long long *)next_task, 1ull);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= ntask) break;
+        const int64_t task = task_list ? (int64_t)task_list[slot] : slot;
         const int64_t p = task >> 2;
         const int seed = (int)((task >> 1) & 1), left = (int)(task & 1);
         const pastis_cand c = pairs[p];
@@ -314,18 +339,51 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext(const uint8_t *qcodes, c
             const uint8_t *qa = left ? qcodes + qo + pi - 1 : qcodes + qo + pi + k;
             const uint8_t *ta = left ? tcodes + to + pj - 1 : tcodes + to + pj + k;
             const int A = left ? pi : lq - pi - k, B = left ? pj : lt - pj - k, st = left ? -1 : 1;
-            if (!xd_diag_warp(qa, A, st, ta, B, st, s_mat, o, e, X, &r))
-                xd_extend_warp(qa, A, st, ta, B, st, s_mat, o, e, X, buf, W, &r);
+            if (!xd_diag_warp<CARRY>(qa, A, st, ta, B, st, s_mat, o, e, X, &r))
+                xd_extend_warp<CARRY>(qa, A, st, ta, B, st, s_mat, o, e, X, buf, W, &r);
         }
         if (lane == 0) out[task] = r;
         __syncwarp();
     }
 }
 
+// The filter-only mode between its phases: a seed whose alignment (spans known from the
+// extension ends alone) leaves less than the coverage bound on the shorter sequence
+// cannot pass, so its extensions need no carried statistics; the others (both
+// directions of a seed that covers enough) are flagged for the second phase.  Zero past
+// the batch, so a scan over the capacity counts the batch's tasks.
+__global__ void k_xd_mark(const int64_t *qoffsets, const int64_t *toffsets, const pastis_cand *pairs, int64_t n,
+                          int k, int cov, const ext_out *ext, uint32_t *need, const int64_t *dn, const int *chk) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t f[2] = {0u, 0u};
+    if (!(dn && p >= *dn) && !(chk && (chk[0] | chk[1]))) {
+        const pastis_cand c = pairs[p];
+        const int lq = (int)(qoffsets[c.i + 1] - qoffsets[c.i]), lt = (int)(toffsets[c.j + 1] - toffsets[c.j]);
+        const int ns = (c.count >= 2 && c.qpos[1] != 0xFFFF) ? 2 : 1;
+        for (int s = 0; s < ns; ++s) {
+            const ext_out R = ext[p * 4 + s * 2 + 0], L = ext[p * 4 + s * 2 + 1];
+            const int span = lq <= lt ? L.a + k + R.a : L.b + k + R.b;
+            f[s] = 100 * span >= cov * min(lq, lt) ? 1u : 0u;
+        }
+    }
+    need[p * 4 + 0] = f[0]; need[p * 4 + 1] = f[0];
+    need[p * 4 + 2] = f[1]; need[p * 4 + 3] = f[1];
+}
+
+// The flagged tasks in order, and their count after them (list[n4]).
+__global__ void k_xd_tasks(const uint32_t *need, const uint32_t *off, int64_t n4, uint32_t *list) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n4) return;
+    if (need[t]) list[off[t]] = (uint32_t)t;
+    if (t == n4 - 1) list[n4] = off[t] + need[t];
+}
+
 __global__ void k_xd_combine(const uint8_t *qcodes, const int64_t *qoffsets, const uint8_t *tcodes,
                              const int64_t *toffsets, const pastis_cand *pairs,
-                             int64_t n_pairs, int k, const int8_t *gmat, int ani, int cov, const ext_out *ext,
-                             pastis_aln *out, unsigned long long *cells, const int64_t *dn, const int *chk) {
+                             int64_t n_pairs, int k, const int8_t *gmat, int ani, int cov, int filtered,
+                             const ext_out *ext, pastis_aln *out, unsigned long long *cells, const int64_t *dn,
+                             const int *chk) {
     if (dn) n_pairs = *dn;
     if (chk && (chk[0] | chk[1])) return;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,6 +424,9 @@ __global__ void k_xd_combine(const uint8_t *qcodes, const int64_t *qoffsets, con
             if (take) { best = cur; best_ok = ok; }
             my += (unsigned long long)(L.cells + R.cells);
         }
+        // the filter-only mode: a pair that fails keeps its score and end (a seed that
+        // failed the coverage test has no carried statistics)
+        if (filtered && !best_ok) { best.qb = best.tb = 0; best.ident = best.cols = 0; }
         out[p] = best;
     }
     if (cells) {
@@ -434,7 +495,8 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     memcpy(hconst + 640, ctx->sw_lay.extra, PASTIS_SW_BINS);
     if (!g) PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, hconst, sizeof(hconst), cudaMemcpyHostToDevice, st));
     PASTIS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64, st));
-    const int xd = params->mode == PASTIS_XD;
+    const int xd = params->mode == PASTIS_XD || params->mode == PASTIS_XD_FILTERED;
+    const int xd_filtered = params->mode == PASTIS_XD_FILTERED;
     const int64_t *dn = g ? g->dc : nullptr;
     const int *chk = g ? flags + 4 : nullptr;
     if (g) {
@@ -479,13 +541,15 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
         lmax = hf[2];
     }
     if (lmax > PASTIS_MAX_LEN) return PASTIS_ERR_INVALID_ARG;
-    int xd_per_sm = 2;
+    int xd_per_sm = 2, xd1_per_sm = 2;        // CTAs per SM with carries, and without (fewer registers)
     if (xd) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xd_per_sm, k_xd_ext, ALN_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xd_per_sm, k_xd_ext<true>, ALN_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xd1_per_sm, k_xd_ext<false>, ALN_THREADS, 0);
         if (xd_per_sm < 1) xd_per_sm = 1;
+        if (xd1_per_sm < xd_per_sm) xd1_per_sm = xd_per_sm;
     }
-    const int blocks = ctx->sm_count * xd_per_sm;
-    const int nwarps = blocks * ALN_WARPS;
+    const int blocks = ctx->sm_count * xd_per_sm, blocks1 = ctx->sm_count * xd1_per_sm;
+    const int nwarps = (xd_filtered ? blocks1 : blocks) * ALN_WARPS;     // per-warp fallback buffers
     if (!xd) {
         s = sw_align(ctx, d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params, dmat, flags, lmax,
                      d_out, d_cells, dn, chk);
@@ -496,16 +560,48 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
         PASTIS_WS(gbuf, ctx, WS_ALN_SCRATCH, sizeof(int32_t) * 18 * (size_t)W * nwarps);
         ext_out *ext;
         PASTIS_WS(ext, ctx, WS_ALN_PASS1, sizeof(ext_out) * 4 * (size_t)n_pairs);
-        prof_begin(ctx, "xd_extend");
-        k_xd_ext<<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs,
-                                                 params->k, dmat, params->gap_open, params->gap_extend, params->xdrop,
-                                                 gbuf, W, flags + 6, ext, dn, chk);
-        PASTIS_LAUNCHED(ctx);
-        prof_end(ctx);
+        if (!xd_filtered) {
+            prof_begin(ctx, "xd_extend");
+            k_xd_ext<true><<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                           n_pairs, params->k, dmat, params->gap_open,
+                                                           params->gap_extend, params->xdrop, gbuf, W, flags + 6, ext,
+                                                           nullptr, nullptr, dn, chk);
+            PASTIS_LAUNCHED(ctx);
+            prof_end(ctx);
+        } else {
+            // phase 1: every extension's score, end and cells; then the carried
+            // statistics only for the seeds whose spans pass the coverage test
+            const int64_t n4 = 4 * n_pairs;
+            uint32_t *need;
+            PASTIS_WS(need, ctx, WS_ALN_ORDER, sizeof(uint32_t) * (3 * (size_t)n4 + 4));
+            uint32_t *off = need + n4, *list = off + n4 + 1;
+            prof_begin(ctx, "xd_extend");
+            k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                            n_pairs, params->k, dmat, params->gap_open,
+                                                            params->gap_extend, params->xdrop, gbuf, W, flags + 6,
+                                                            ext, nullptr, nullptr, dn, chk);
+            PASTIS_LAUNCHED(ctx);
+            prof_end(ctx);
+            k_xd_mark<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_qoffsets, d_toffsets, d_pairs, n_pairs,
+                                                                          params->k, params->cov_min_pct, ext, need,
+                                                                          dn, chk);
+            PASTIS_LAUNCHED(ctx);
+            s = exclusive_scan_u32(ctx, need, off, n4);
+            if (s != PASTIS_OK) return s;
+            k_xd_tasks<<<(unsigned)ceil_div64(n4, 256), 256, 0, st>>>(need, off, n4, list);
+            PASTIS_LAUNCHED(ctx);
+            prof_begin(ctx, "xd_carry");
+            k_xd_ext<true><<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                           n_pairs, params->k, dmat, params->gap_open,
+                                                           params->gap_extend, params->xdrop, gbuf, W, flags + 12,
+                                                           ext, list, list + n4, dn, chk);
+            PASTIS_LAUNCHED(ctx);
+            prof_end(ctx);
+        }
         prof_begin(ctx, "xd_combine");
         k_xd_combine<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(
             d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat, params->ani_min_pct,
-            params->cov_min_pct, ext, d_out, (unsigned long long *)d_cells, dn, chk);
+            params->cov_min_pct, xd_filtered, ext, d_out, (unsigned long long *)d_cells, dn, chk);
         PASTIS_LAUNCHED(ctx);
         prof_end(ctx);
     }

@@ -185,7 +185,8 @@ pastis_status check_params(const pastis_params *p) {
     if (p->m_subs < 0 || p->m_subs > PASTIS_MAX_M) return PASTIS_ERR_INVALID_ARG;
     if (p->m_subs > ipow24(p->k) - 1) return PASTIS_ERR_INVALID_ARG;
     if (p->min_shared < 1) return PASTIS_ERR_INVALID_ARG;
-    if (p->mode != PASTIS_SW && p->mode != PASTIS_XD && p->mode != PASTIS_SW_SCORE && p->mode != PASTIS_SW_FILTERED)
+    if (p->mode != PASTIS_SW && p->mode != PASTIS_XD && p->mode != PASTIS_SW_SCORE && p->mode != PASTIS_SW_FILTERED &&
+        p->mode != PASTIS_XD_FILTERED)
         return PASTIS_ERR_INVALID_ARG;
     if (p->xdrop < 0 || p->xdrop > 1000000) return PASTIS_ERR_INVALID_ARG;
     if (p->gap_open < 0 || p->gap_extend < 0 || p->gap_open > 1000 || p->gap_extend > 1000)

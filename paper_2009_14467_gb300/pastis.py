@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
-SW, XD, SW_SCORE, SW_FILTERED = 0, 1, 2, 3
+SW, XD, SW_SCORE, SW_FILTERED, XD_FILTERED = 0, 1, 2, 3, 4
 SW_BINS, SW_BIN_WIDTH, SW_MAX_EXTRA = 64, 32, 2     # pass-1 layout per query-length bin
 SW_INT32 = 3                                        # a layout value: the bin's pairs in 32-bit lanes
 

@@ -383,3 +383,24 @@ def test_align_filtered_parity(P, ctx, which):
     sw, _, _, _ = _align_both(P, ctx, ps, cands, P.SW)
     assert O.filter_edges(ps.offsets, cands, got).tobytes() == O.filter_edges(ps.offsets, cands, sw).tobytes()
 
+
+@pytest.mark.parametrize("X", [0, 5, 49, 1000])
+def test_xd_filtered_parity(P, ctx, X):
+    """PASTIS_XD_FILTERED (extensions without carried statistics first, then again with
+    them for the seeds that cover enough) against the oracle's mode 4, every field; the
+    edges equal those of PASTIS_XD."""
+    ps = synth.families_1k()
+    cands = _cands(P, ctx, ps)[1]
+    got, want, gc, wc = _align_both(P, ctx, ps, cands, P.XD_FILTERED, xdrop=X)
+    assert gc == wc
+    _cmp_alns(got, want)
+    xd, _, _, _ = _align_both(P, ctx, ps, cands, P.XD, xdrop=X)
+    assert O.filter_edges(ps.offsets, cands, got).tobytes() == O.filter_edges(ps.offsets, cands, xd).tobytes()
+
+
+def test_xd_filtered_substitute_seeds(P, ctx):
+    ps = synth.zipf_100k(n=2000).subset(np.arange(300))
+    cands = _cands(P, ctx, ps, m=25)[1]
+    got, want, gc, wc = _align_both(P, ctx, ps, cands, P.XD_FILTERED)
+    assert gc == wc
+    _cmp_alns(got, want)

@@ -299,3 +299,22 @@ def test_filtered_mode_keeps_what_the_filter_needs():
         assert (fl[f][~ok] == 0).all()
     assert O.filter_edges(ps.offsets, c, fl).tobytes() == O.filter_edges(ps.offsets, c, sw).tobytes()
 
+
+def test_filtered_xd_mode_keeps_what_the_filter_needs():
+    """Mode 4 (x-drop for the filter only): a passing pair's record is XD's, a failing
+    pair keeps XD's score, end and seed with the rest 0, and the edges are XD's."""
+    ps = synth.families_1k()
+    codes = O.encode(ps.ascii)
+    rp, code, pos = O.kmers(codes, ps.offsets, 6)
+    c = O.candidates(rp, code, pos, 6, 0, MAT, 1)[:1500]
+    xd, cx = O.align_pairs(codes, ps.offsets, c, MAT, mode=O.XD)
+    fl, cf = O.align_pairs(codes, ps.offsets, c, MAT, mode=O.XD_FILTERED)
+    assert cx == cf
+    ok = xd['passes'] == 1
+    assert 0 < ok.sum() < len(c)
+    assert fl[ok].tobytes() == xd[ok].tobytes()
+    for f in ("score", "qe", "te", "seed_used"):
+        assert (fl[f] == xd[f]).all()
+    for f in ("qb", "tb", "ident", "cols", "passes"):
+        assert (fl[f][~ok] == 0).all()
+    assert O.filter_edges(ps.offsets, c, fl).tobytes() == O.filter_edges(ps.offsets, c, xd).tobytes()
