@@ -1,7 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py times:
 the 100,000-protein set with 25 substitute k-mers and Smith-Waterman (one of 8
 equal-work query-row blocks) and the 1,000,000-protein set with exact k-mers and x-drop
-(one of 64 blocks).  The oracle cannot run these jobs whole, so outputs are sampled
+(one of 64 blocks), each in the bench's alignment mode (the filter-only forms).  The oracle cannot run these jobs whole, so outputs are sampled
 and checked one by one:
  * candidate records: each sampled (i, j) against the oracle's product over the two
    sequences alone (a pair's semiring value depends on its two rows only);
