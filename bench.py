@@ -762,6 +762,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefilter", action="store_true", help="plain mode: skip the learned-prefilter leg")
     ap.add_argument("--no-xd-leg", action="store_true", help="plain mode: skip the 1M-protein x-drop leg")
+    ap.add_argument("--no-graph-leg", action="store_true",
+                    help="x-drop workloads: skip the block replayed from a captured CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-1 layout (no tuner)")
     ap.add_argument("--tune-pairs", type=int, default=3_000_000, help="candidates the tuner samples")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
@@ -1019,6 +1021,39 @@ def main():
                     "gcups": int(c_sw.item()) / t / 1e9,
                     "sample": "all candidates of row block 0 of the job (a fixed, seeded block of query rows)"}
 
+    graph_leg = None
+    if w["mode"] in (1, 4) and rank == 0 and not args.no_graph_leg:
+        # the same block's x-drop alignment replayed from a captured CUDA graph (an
+        # alignment plan: the whole set resident as targets, the block's rows as the query
+        # batch) against the direct call: records equal, time of each
+        def ev_time(fn):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return out, e0.elapsed_time(e1) / 1000.0
+
+        i0, i1 = blocks[0]
+        r0, r1 = int(ps.offsets[i0]), int(ps.offsets[i1])
+        q_offs = (ps.offsets[i0:i1 + 1] - r0).astype(np.int64)
+        q_pairs = cands.clone()
+        q_pairs.view(torch.int32)[:, 0] -= i0                  # query index within the batch
+        lmax = int(np.diff(ps.offsets).max())
+        plan = P.AlignPlan(ctx, codes, offs_dev, params, i1 - i0, r1 - r0, int(cands.shape[0]), lmax)
+        try:
+            P.align_pairs(ctx, codes, offs_dev, cands, params)            # warm-up of both
+            plan.run(codes[r0:r1], q_offs, q_pairs)
+            direct, t_direct = ev_time(lambda: P.align_pairs(ctx, codes, offs_dev, cands, params))
+            replay, t_graph = ev_time(lambda: plan.run(codes[r0:r1], q_offs, q_pairs))
+            graph_leg = {"pairs": int(cands.shape[0]), "graph_nodes": plan.graph_nodes, "s_graph": t_graph,
+                         "s_direct": t_direct, "records_equal": bool(torch.equal(replay, direct)),
+                         "note": ("one graph launch per block (the plan copies the batch in and the records out) "
+                                  "against the direct call's launches and synchronisations")}
+        finally:
+            plan.close()
+
     pref = None
     if w["mode"] not in (1, 4) and not args.no_prefilter and batches >= 5 and world == 1:
         # the learned prefilter against the plain path on this set (bounded: trained on
@@ -1077,7 +1112,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof, "roofline_spgemm": roof_spg, "dominant_kernel": dominant, "int_probe": probe_line,
             "kernel_ms_timed_region": kernel_ms,
-            "sw_on_block": sw_block, "autotune": tune,
+            "sw_on_block": sw_block, "graph_on_block": graph_leg, "autotune": tune,
             "xdrop_1m": xd,
             "prefilter_speedup": pref["speedup"] if pref else None,
             "edge_recall": pref["edge_recall"] if pref else None, "prefilter": pref,
