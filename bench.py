@@ -373,7 +373,26 @@ def start_set_generation(name):
     return fut
 
 
-def xd_leg(P, dev, word_rate, n_sm, clk_mhz, n_blocks=2, pending=None):
+def xd_roofline(cells, ms, per_warp, half_rate, word_rate, n_sm, clk_mhz):
+    """Roofline of the x-drop extensions' first phase for one launch of `cells` computed
+    cells in `ms`: against the measured 16x2 peak when they run in 16-bit lanes
+    (per_warp > 0), else the measured 32-bit peak."""
+    achieved = cells * OPS_PER_CELL / (ms / 1000.0) / 1e12
+    if per_warp:
+        peak = n_sm * half_rate * 32 * HALVES_PER_LANE * clk_mhz * 1e6 / 1e12
+        note = (f"measured: {n_sm} SMs x {half_rate:.3f} warp-instructions/clk/SM (best 16x2 kind of the probe) "
+                f"x 32 lanes x {HALVES_PER_LANE} halves x {clk_mhz:.0f} MHz; 16-bit lanes, {per_warp} extensions per warp")
+    else:
+        peak = n_sm * word_rate * 32 * clk_mhz * 1e6 / 1e12
+        note = (f"measured: {n_sm} SMs x {word_rate:.3f} warp-instructions/clk/SM (best 32-bit kind of the probe) "
+                f"x 32 lanes x {clk_mhz:.0f} MHz; 32-bit lanes")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "xd_extend", "peak_note": note, "ops_per_cell": OPS_PER_CELL,
+            "cells": "computed cells of the x-drop extensions",
+            "cells_per_clk_sm": cells / (ms / 1000.0) / (n_sm * clk_mhz * 1e6)}
+
+
+def xd_leg(P, dev, half_rate, word_rate, n_sm, clk_mhz, n_blocks=2, pending=None, tune_pairs=1_000_000):
     """The 1,000,000-protein exact-k-mer x-drop configuration on a bounded sample: one
     warm-up row block, then `n_blocks` timed row blocks of its 64 (each the whole path:
     encode, A, candidates, x-drop alignment from both seeds, filter).  `pending`: the
@@ -391,7 +410,13 @@ def xd_leg(P, dev, word_rate, n_sm, clk_mhz, n_blocks=2, pending=None):
     batches = default_batches(ps.n)
     blocks = row_blocks(ps.n, batches)
     cells = torch.zeros(1, dtype=torch.int64, device=dev)
-    P.run(ctx, a, o, params, rows=blocks[0])
+    r0 = P.run(ctx, a, o, params, rows=blocks[0])
+    # extensions per warp, tuned on a sample of block 0's candidates (every stride-th query)
+    cands0 = r0["cands"]
+    stride = max(1, -(-cands0.shape[0] // tune_pairs))
+    sample = cands0[(cands0.view(torch.int32).view(-1, 5)[:, 0] % stride) == 0].contiguous()
+    pw, tms = P.autotune_xd(ctx, r0["codes"], o, sample, params, reps=2)
+    del r0, cands0, sample
     torch.cuda.synchronize()
     ctx.profile(True)
     ms = 0.0
@@ -415,13 +440,12 @@ def xd_leg(P, dev, word_rate, n_sm, clk_mhz, n_blocks=2, pending=None):
            "candidates_per_block": cands // n_blocks, "edges_per_block": edges // n_blocks,
            "set_wait_s": round(gen_s, 1),
            "kernel_ms": {k: round(v[1], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]}}
+    out["xd_per_warp"] = pw
+    out["xd_tuner_ms"] = {("32-bit lanes" if c == 0 else f"16-bit lanes, {c} per warp"): round(v, 3)
+                          for c, v in tms.items()}
     if "xd_extend" in prof:
         n_l, ms_l = prof["xd_extend"]
-        ach = total_cells / max(1, n_l) * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
-        peak = n_sm * word_rate * 32 * clk_mhz * 1e6 / 1e12
-        out["roofline"] = {"bound": "alu", "kernel": "xd_extend", "achieved": ach, "peak": peak, "unit": "Tops/s",
-                           "frac": ach / peak, "ops_per_cell": OPS_PER_CELL,
-                           "peak_note": f"measured: {n_sm} SMs x {word_rate:.3f} warp-instructions/clk/SM x 32 lanes"}
+        out["roofline"] = xd_roofline(total_cells / max(1, n_l), ms_l / n_l, pw, half_rate, word_rate, n_sm, clk_mhz)
     ctx.close()
     return out
 
@@ -764,7 +788,7 @@ def main():
     ap.add_argument("--no-xd-leg", action="store_true", help="plain mode: skip the 1M-protein x-drop leg")
     ap.add_argument("--no-graph-leg", action="store_true",
                     help="x-drop workloads: skip the block replayed from a captured CUDA graph")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-1 layout (no tuner)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default alignment layouts (no tuner)")
     ap.add_argument("--tune-pairs", type=int, default=3_000_000, help="candidates the tuner samples")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel profile here")
     ap.add_argument("--probe-iters", type=int, default=20000, help="probe mode: loop iterations per kernel")
@@ -868,6 +892,24 @@ def main():
                            for b in np.flatnonzero(extra)},
                 "int32_vs_int16_cycles": round(float(cyc[P.pastis.SW_INT32].sum()) / max(1.0, float(cyc[0].sum())), 3),
                 "pass1_cycles_saved_on_sample": round(1.0 - chosen / base, 4) if base > 0 else 0.0}
+        del codes, A, cands, qi, sample
+
+    if w["mode"] == 4 and not args.no_autotune:
+        # setup, untimed: x-drop extensions per warp (16-bit lanes) or 32-bit lanes, tuned
+        # on the candidates of every stride-th query of block 0
+        t0 = time.perf_counter()
+        codes = P.encode(ctx, ascii_dev)
+        A = P.build_kmers(ctx, codes, offs_dev, 6)
+        cands = P.overlap_spgemm(ctx, A, params, rows=blocks[0])
+        stride = max(1, -(-cands.shape[0] // args.tune_pairs))
+        qi = cands.view(torch.int32).view(-1, 5)[:, 0]
+        sample = cands[(qi % stride) == 0].contiguous()
+        pw, tms = P.autotune_xd(ctx, codes, offs_dev, sample, params, reps=2)
+        torch.cuda.synchronize()
+        tune = {"sample_pairs": int(sample.shape[0]), "sample": f"candidates of every {stride}th query of block 0",
+                "setup_s": round(time.perf_counter() - t0, 2), "xd_per_warp": pw,
+                "xd_ms_by_setting": {("32-bit lanes" if c == 0 else f"16-bit lanes, {c} per warp"): round(v, 3)
+                                     for c, v in tms.items()}}
         del codes, A, cands, qi, sample
 
     # the integer-pipe peak, measured on this GPU (warp-instructions per SM clock of each
@@ -974,15 +1016,10 @@ def main():
                 "recurrence_mix_cells_per_clk_sm": probe_line["sw_mix_cells_per_clk_sm"]}
 
     if "xd_extend" in prof and "sw_pass1" not in prof:
-        # x-drop: int32 recurrence with carries, computed live cells
+        # x-drop: the extensions' first phase, computed cells
         n_l, ms_l = prof["xd_extend"]
-        achieved = total_cells / max(1, n_l) * OPS_PER_CELL / (ms_l / n_l / 1000.0) / 1e12
-        peak = n_sm * word_rate * 32 * clk_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "xd_extend",
-                "peak_note": (f"measured: {n_sm} SMs x {word_rate:.3f} warp-instructions/clk/SM (best 32-bit kind "
-                              f"of the probe) x 32 lanes x {clk_mhz:.0f} MHz"),
-                "ops_per_cell": OPS_PER_CELL, "cells": "computed cells of the x-drop extensions"}
+        roof = xd_roofline(total_cells / max(1, n_l), ms_l / n_l, ctx.xd_layout() if w["mode"] == 4 else 0,
+                           half_rate, word_rate, n_sm, clk_mhz)
     # roofline of the overlap product (HBM bound): algorithmic bytes = 16 per left-operand
     # entry (its code, position and posting-list bounds), 8 per product (the posting
     # entry gathered), 20 per candidate record written
@@ -1072,7 +1109,7 @@ def main():
     xd = None
     if w["mode"] not in (1, 4) and not args.no_xd_leg and world == 1:
         # the 1,000,000-protein x-drop configuration, bounded to three row blocks
-        xd = xd_leg(P, dev, word_rate, n_sm, clk_mhz, pending=xd_set)
+        xd = xd_leg(P, dev, half_rate, word_rate, n_sm, clk_mhz, pending=xd_set)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

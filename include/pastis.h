@@ -342,6 +342,37 @@ pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const
                                  const pastis_params *params, int32_t reps, uint8_t *h_extra,
                                  int64_t *h_cycles);
 
+/* ---- batching: the x-drop lane layout -------------------------------------------------
+ * The first phase of PASTIS_XD_FILTERED (the score, end and cells of every extension of
+ * Sec. IV-E's x-drop, before the carried statistics) runs in 16-bit lanes with
+ * `per_warp` extensions side by side in each warp (1, 2 or 4: one window of 128
+ * diagonals over 32, 16 or 8 lanes), or in 32-bit lanes, one extension per warp
+ * (per_warp = 0).  Extensions the 16-bit form cannot hold run in 32-bit lanes whatever
+ * the setting: gap open or extend above 128, X above 30,000, the largest substitution
+ * score times the shorter side of the extension above 30,000, a side of length 0, or a
+ * computed antidiagonal wider than 64 cells.  A speed choice only: every output is the
+ * same under every setting.  A context starts with PASTIS_XD_DEFAULT_PER_WARP.
+ * pastis_xd_layout_set gives PASTIS_ERR_INVALID_ARG for any other value and leaves the
+ * setting unchanged; pastis_xd_layout_get returns it (-1 for a NULL context).        */
+#define PASTIS_XD_DEFAULT_PER_WARP 4
+pastis_status pastis_xd_layout_set(pastis_ctx *ctx, int32_t per_warp);
+int32_t pastis_xd_layout_get(const pastis_ctx *ctx);
+
+/* The x-drop layout tuner: runs the filter-only x-drop of the given pairs (the arguments
+ * of pastis_align_pairs_qt; a sample of the workload's candidates) under each setting,
+ * 0, 1, 2 and 4, `reps` times each, every call timed by CUDA events on the context's
+ * stream.  The fastest setting is set on the context when it beats the current one by
+ * 2% or more (else the current one stays) and copied to *h_per_warp (optional); h_ms
+ * (optional, host, 4 doubles) receives each setting's best time in milliseconds, in
+ * the order 0, 1, 2, 4.  params->mode must be PASTIS_XD or PASTIS_XD_FILTERED
+ * (PASTIS_ERR_UNSUPPORTED otherwise).  Validation and errors as
+ * pastis_align_pairs_qt; the setting is unchanged on error.  Synchronises.          */
+pastis_status pastis_autotune_xd(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                 int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                 int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
+                                 const pastis_params *params, int32_t reps, int32_t *h_per_warp,
+                                 double *h_ms);
+
 /* ---- batching: alignment plans replayed as CUDA graphs ------------------------------
  * A plan captures the whole alignment of one batch (the input checks, then pass 1-3 of
  * PASTIS_SW / PASTIS_SW_SCORE or the x-drop extensions and their combination) once, as

@@ -298,6 +298,324 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
     return true;
 }
 
+// ---------------------------------------------------------------------------------
+// The same extensions in 16-bit lanes, several per warp (the first phase of the
+// filter-only mode: score, end and cells, no carried statistics).
+//
+// The diagonal window of xd_diag_warp (128 diagonals, at most 64 computed cells per
+// antidiagonal) is split over G = 32 / R lanes, so a warp runs R extensions side by
+// side, each in a segment of G lanes.  Lane s of a segment owns the 4R diagonals
+// kbase + 4R s .. kbase + 4R s + 4R - 1; on antidiagonal d it computes the 2R cells of
+// d's parity, in R registers of two signed 16-bit halves: register r of the even set
+// holds the diagonals at offsets 4r and 4r + 2, of the odd set 4r + 1 and 4r + 3.  A
+// lane's cells of one antidiagonal are consecutive rows a0 .. a0 + 2R - 1, so their
+// query and target residues are windows that slide by one residue every second
+// antidiagonal; the windows hold each residue as its offset into a score table of
+// which every lane of the warp has its own copy in its own shared-memory bank.  Per
+// register and antidiagonal the recurrence is the packed one of the Smith-Waterman
+// pass 1 without the floor at 0: E and F as __viaddmax_s16x2, the diagonal as
+// __vadd2, H as __vimax3_s16x2.  The x-drop test (H >= best - X) and the computed range
+// [clo, chi] become a per-half mask by clamps alone: min(max(H, lim - 1), lim) - lim
+// is -1 exactly where H < lim, min(row - clo, chi - row) is negative exactly outside
+// the range, and the mask selects the dead value.
+//
+// Dead cells hold XD16_NEG in H, E and F.  Live values lie in [best - X - o - e, best
+// + the largest substitution score], values derived from dead ones in [XD16_NEG - o -
+// e, XD16_NEG + 63], and every one of them is pruned (XD16_NEG + 63 < -X), so no sum
+// wraps when X, the best score and o + e stay within the bounds checked below; an
+// extension outside them, or whose computed range outgrows the window, is listed for
+// the 32-bit kernel, which computes it from the start.
+//
+// Every lane runs every step, an odd antidiagonal and an even one per turn of one
+// loop, so the segments' parities agree and the packed sources need no per-segment
+// branch; a segment whose extension has ended computes on empty ranges and writes
+// nothing until it takes the next extension at the top of the loop.  The end cell is
+// found once per extension: the step that raises the best score keeps a copy of its
+// H registers, and the first row holding the best is read from that copy at the end.
+// ---------------------------------------------------------------------------------
+constexpr int XD16_NEG = -32512;                 // 0x8100
+constexpr uint32_t XD16_NEG2 = (uint32_t)(XD16_NEG & 0xffff) * 0x10001u;   // 0x81008100
+constexpr int XD16_LIM = 30000;                  // bound on X and on an extension's best score
+// Score table, int16: byte offset q * 1536 + (t >> 1) * 128 + (t & 1) * 2 + 4 * lane holds
+// s(q, t) for every lane, so lane L always reads bank L.
+constexpr int XD16_TAB = PASTIS_NSYM * PASTIS_NSYM * 32;   // entries
+constexpr uint32_t XD16_QOFF = PASTIS_NSYM / 2 * 128;      // bytes per query residue
+
+// Whether the 16-bit kernel may run an x-drop with these penalties at all.
+static inline bool xd16_params_fit(int o, int e, int X) { return o <= 128 && e <= 128 && X <= XD16_LIM; }
+
+__device__ __forceinline__ uint32_t xd16_pk(int v) { return (uint32_t)(v & 0xffff) * 0x10001u; }
+
+template <int R>
+struct xd16_ext {
+    uint32_t H[2][R], E[2][R], F[2][R];          // [parity of the diagonals][register]
+    uint32_t QW[R], TW[R];                       // cells 2r (low half), 2r + 1: table offsets of q and t
+    uint32_t HS[R];                              // H of the antidiagonal sd that last raised best
+    const uint8_t *q, *t;
+    int st, A, B;                                // A = B = 0 while the segment has no extension
+    int d, best, sd, sa0, llo, lhi, kbase;
+    long long cells;
+    int64_t task;
+    bool active;
+};
+
+// Table offset of query residue idx (0 outside the sequence), and of target residue idx
+// plus this lane's column.
+template <int R>
+__device__ __forceinline__ uint32_t xd16_qoff(const xd16_ext<R> &x, int idx) {
+    return (unsigned)idx < (unsigned)x.A ? (uint32_t)x.q[(long long)idx * x.st] * XD16_QOFF : 0u;
+}
+template <int R>
+__device__ __forceinline__ uint32_t xd16_toff(const xd16_ext<R> &x, int idx, uint32_t lane4) {
+    uint32_t c = (unsigned)idx < (unsigned)x.B ? (uint32_t)x.t[(long long)idx * x.st] : 0u;
+    return (c >> 1) * 128u + (c & 1u) * 2u + lane4;
+}
+
+// The windows for antidiagonal d whose first row in this lane is a0: cell j has query
+// residue a0 + j - 1 and target residue d - a0 - j - 1.
+template <int R>
+__device__ __forceinline__ void xd16_load_windows(xd16_ext<R> &x, int d, int a0, uint32_t lane4) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        x.QW[r] = xd16_qoff(x, a0 + 2 * r - 1) | (xd16_qoff(x, a0 + 2 * r) << 16);
+        x.TW[r] = xd16_toff(x, d - a0 - 2 * r - 1, lane4) | (xd16_toff(x, d - a0 - 2 * r - 2, lane4) << 16);
+    }
+}
+
+// One antidiagonal (d = x.d + 1, of parity PAR) of the segment's extension, run by every
+// lane of the warp.
+template <int R, int PAR>
+__device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask, int sbase, const char *tab,
+                                          uint32_t lane4, uint32_t o2, uint32_t ne2, int X, ext_out *out,
+                                          uint32_t *ovf_list, uint32_t *ovf_n) {
+    constexpr int G = 32 / R, WD = 4 * R, NC = 2 * R;
+    constexpr int P = PAR, Q = 1 - PAR;
+    const int d = x.d + 1;
+    const int clo = max(max(x.llo, d - x.B), 0);
+    const int chi = min(min(x.lhi + 1, x.A), d);
+    const bool empty = clo > chi;                        // the extension ended (d > A + B included)
+    bool defer = !empty && chi - clo + 1 > G * NC;
+    // the computed range's diagonals, with their E and F predecessors, inside the window
+    const int kmin = 2 * clo - d - 1, kmax = 2 * chi - d + 1;
+    const bool move = !empty && !defer && (kmin < x.kbase || kmax > x.kbase + 127);
+    int a0 = (d + x.kbase + WD * ls + P) >> 1;          // this lane's first row on d
+    if (P == 1) {        // rows moved on by one: a new last query residue
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            x.QW[r] = __byte_perm(x.QW[r], r == R - 1 ? xd16_qoff(x, a0 + NC - 2) : x.QW[r + 1], 0x5432);
+    } else {             // columns moved on by one: a new first target residue
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r)
+            x.TW[r] = __byte_perm(r == 0 ? xd16_toff(x, d - a0 - 1, lane4) << 16 : x.TW[r - 1], x.TW[r], 0x5432);
+    }
+    if (__any_sync(0xffffffffu, move)) {
+        if (move) {
+            const int sh = ((kmin + kmax) / 2 - (x.kbase + 64)) / WD;      // whole lanes, centring the range
+            x.kbase += WD * sh;
+            if (kmin < x.kbase || kmax > x.kbase + 127) {
+                defer = true;
+            } else {
+                const int src = ls + sh;
+                const bool in = (unsigned)src < (unsigned)G;
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t h = __shfl_sync(smask, x.H[p][r], src & (G - 1), G);
+                        const uint32_t ee = __shfl_sync(smask, x.E[p][r], src & (G - 1), G);
+                        const uint32_t ff = __shfl_sync(smask, x.F[p][r], src & (G - 1), G);
+                        x.H[p][r] = in ? h : XD16_NEG2;
+                        x.E[p][r] = in ? ee : XD16_NEG2;
+                        x.F[p][r] = in ? ff : XD16_NEG2;
+                    }
+                a0 = (d + x.kbase + WD * ls + P) >> 1;
+                xd16_load_windows(x, d, a0, lane4);
+            }
+        }
+    }
+    const int lim = x.best - X;
+    const uint32_t lim2 = xd16_pk(lim), limm2 = xd16_pk(lim - 1);
+    const uint32_t span2 = xd16_pk(chi - clo), rb2 = xd16_pk(a0 - clo);
+    // the sources on d - 1 that cross a lane boundary
+    uint32_t bh, bx;
+    if (P == 0) {        // F of the first cell: the previous lane's last odd diagonal
+        bh = __shfl_up_sync(0xffffffffu, x.H[Q][R - 1], 1, G);
+        bx = __shfl_up_sync(0xffffffffu, x.F[Q][R - 1], 1, G);
+        if (ls == 0) { bh = XD16_NEG2; bx = XD16_NEG2; }
+    } else {             // E of the last cell: the next lane's first even diagonal
+        bh = __shfl_down_sync(0xffffffffu, x.H[Q][0], 1, G);
+        bx = __shfl_down_sync(0xffffffffu, x.E[Q][0], 1, G);
+        if (ls == G - 1) { bh = XD16_NEG2; bx = XD16_NEG2; }
+    }
+    uint32_t lbw = 0u;                           // live cells: bit r = cell 2r, bit 16 + r = cell 2r + 1
+    uint32_t hmax = XD16_NEG2;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        uint32_t eh, ex, fh, fx;
+        if (P == 0) {
+            eh = x.H[Q][r]; ex = x.E[Q][r];
+            fh = __byte_perm(r == 0 ? bh : x.H[Q][r - 1], x.H[Q][r], 0x5432);
+            fx = __byte_perm(r == 0 ? bx : x.F[Q][r - 1], x.F[Q][r], 0x5432);
+        } else {
+            fh = x.H[Q][r]; fx = x.F[Q][r];
+            eh = __byte_perm(x.H[Q][r], r == R - 1 ? bh : x.H[Q][r + 1], 0x5432);
+            ex = __byte_perm(x.E[Q][r], r == R - 1 ? bx : x.E[Q][r + 1], 0x5432);
+        }
+        const uint32_t en = __viaddmax_s16x2(ex, ne2, __vsub2(eh, o2));
+        const uint32_t fn = __viaddmax_s16x2(fx, ne2, __vsub2(fh, o2));
+        // substitution scores of rows a0 + 2r and a0 + 2r + 1 from this lane's table column
+        const uint32_t ix = x.QW[r] + x.TW[r];
+        const uint32_t s0 = *(const uint16_t *)(tab + (ix & 0xffffu));
+        const uint32_t s1 = *(const uint16_t *)(tab + (ix >> 16));
+        const uint32_t hn = __vimax3_s16x2(__vadd2(x.H[P][r], __byte_perm(s0, s1, 0x5410)), en, fn);
+        // dead halves: H < lim, or the row outside [clo, chi]
+        const uint32_t rr = __vadd2(rb2, (uint32_t)((2 * r) | ((2 * r + 1) << 16)));
+        const uint32_t w = __vmins2(rr, __vsub2(span2, rr));
+        const uint32_t d1 = __vsub2(__vmins2(__vmaxs2(hn, limm2), lim2), lim2);
+        const uint32_t dm = __vmins2(d1, __vmaxs2(w, 0xffffffffu));
+        x.H[P][r] = (hn & ~dm) | (XD16_NEG2 & dm);
+        x.E[P][r] = (en & ~dm) | (XD16_NEG2 & dm);
+        x.F[P][r] = (fn & ~dm) | (XD16_NEG2 & dm);
+        lbw |= (~dm & 0x00010001u) << r;
+        hmax = __vmaxs2(hmax, x.H[P][r]);
+    }
+    x.cells += empty ? 0 : chi - clo + 1;
+    x.d = d;
+    const unsigned bal = (__ballot_sync(0xffffffffu, lbw != 0u) >> sbase) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
+    const int myh = max((int)(short)(hmax & 0xffffu), (int)hmax >> 16);
+    const int toph = __reduce_max_sync(smask, myh);
+    const bool raise = !empty && !defer && toph > x.best;
+#pragma unroll
+    for (int r = 0; r < R; ++r) x.HS[r] = raise ? x.H[P][r] : x.HS[r];
+    x.sa0 = raise ? a0 : x.sa0;
+    x.sd = raise ? d : x.sd;
+    x.best = raise ? toph : x.best;
+    const uint32_t lo_b = lbw & 0xffffu, hi_b = lbw >> 16;
+    const int jlo = min(lo_b ? 2 * (__ffs(lo_b) - 1) : NC, hi_b ? 2 * (__ffs(hi_b) - 1) + 1 : NC);
+    const int jhi = max(lo_b ? 2 * (31 - __clz(lo_b)) : -1, hi_b ? 2 * (31 - __clz(hi_b)) + 1 : -1);
+    const int first = __ffs(bal) - 1, last = 31 - __clz(bal);
+    x.llo = __shfl_sync(0xffffffffu, a0 + jlo, first & (G - 1), G);
+    x.lhi = __shfl_sync(0xffffffffu, a0 + jhi, last & (G - 1), G);
+    // the end of the extension, or its hand-over to the 32-bit kernel
+    const bool stop = x.active && (defer || empty || bal == 0u);
+    if (__any_sync(0xffffffffu, stop)) {
+        if (stop) {
+            if (defer) {
+                if (ls == 0) ovf_list[atomicAdd(ovf_n, 1u)] = (uint32_t)x.task;
+            } else {
+                // the first row holding best on the antidiagonal that raised it last
+                unsigned mya = 0xFFFFFFFFu;
+#pragma unroll
+                for (int j = NC - 1; j >= 0; --j) {
+                    const uint32_t v = x.HS[j >> 1];
+                    if (((j & 1) ? (int)v >> 16 : (int)(short)(v & 0xffffu)) == x.best) mya = (unsigned)(x.sa0 + j);
+                }
+                const int ta = (int)__reduce_min_sync(smask, mya);
+                if (ls == 0) {
+                    ext_out res;
+                    res.score = x.best;
+                    res.a = x.best > 0 ? ta : 0;
+                    res.b = x.best > 0 ? x.sd - ta : 0;
+                    res.carry = 0u;
+                    res.cells = x.cells;
+                    out[x.task] = res;
+                }
+            }
+            x.active = false;
+            x.A = 0;
+            x.B = 0;
+        }
+    }
+}
+
+// The filter-only mode's first phase in 16-bit lanes: every task (4 p + 2 seed + left)
+// whose extension fits gets its score, end and cells; the others are listed in
+// ovf_list[*ovf_n] for k_xd_ext<false>.  smax = the largest substitution score.
+template <int R>
+__global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes, const int64_t *qoffsets,
+                                                          const uint8_t *tcodes, const int64_t *toffsets,
+                                                          const pastis_cand *pairs, int64_t n_pairs, int k,
+                                                          const int8_t *gmat, int o, int e, int X, int smax,
+                                                          int *next_task, ext_out *out, uint32_t *ovf_list,
+                                                          uint32_t *ovf_n, const int64_t *dn, const int *chk) {
+    constexpr int G = 32 / R, WD = 4 * R;
+    if (dn) n_pairs = *dn;
+    if (chk && (chk[0] | chk[1])) return;
+    __shared__ uint16_t s_tab[XD16_TAB];
+    for (int i = threadIdx.x; i < XD16_TAB; i += blockDim.x) {
+        // i = q * 768 + (t >> 1) * 64 + lane * 2 + (t & 1)
+        const int q = i / 768, t = ((i % 768) >> 6) * 2 + (i & 1);
+        s_tab[i] = (uint16_t)(int)gmat[q * PASTIS_NSYM + t];
+    }
+    __syncthreads();
+    const char *tab = (const char *)s_tab;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lane4 = 4u * (uint32_t)lane;
+    const int seg = lane / G, ls = lane % G, sbase = seg * G;
+    const unsigned smask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << sbase);
+    const uint32_t o2 = xd16_pk(o), ne2 = xd16_pk(-e);
+    const int64_t ntask = n_pairs * 4;
+    xd16_ext<R> x;
+    x.active = false;
+    x.A = 0; x.B = 0; x.d = 0; x.best = 0; x.sd = 0; x.sa0 = 0; x.llo = 0; x.lhi = 0; x.kbase = -64; x.cells = 0;
+    x.task = 0; x.st = 1; x.q = qcodes; x.t = tcodes;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        x.H[0][r] = x.H[1][r] = x.E[0][r] = x.E[1][r] = x.F[0][r] = x.F[1][r] = XD16_NEG2;
+        x.QW[r] = 0u; x.TW[r] = lane4 | (lane4 << 16); x.HS[r] = XD16_NEG2;
+    }
+    bool exhausted = false;
+    for (;;) {
+        if (__any_sync(0xffffffffu, !x.active && !exhausted)) {
+            while (!x.active && !exhausted) {
+                unsigned long long slot = 0;
+                if (ls == 0) slot = atomicAdd((unsigned long long *)next_task, 1ull);
+                slot = __shfl_sync(smask, slot, 0, G);
+                if ((int64_t)slot >= ntask) { exhausted = true; break; }
+                x.task = (int64_t)slot;
+                const int64_t p = x.task >> 2;
+                const int seed = (int)((x.task >> 1) & 1), left = (int)(x.task & 1);
+                const pastis_cand c = pairs[p];
+                if (!(seed == 0 || (c.count >= 2 && c.qpos[1] != 0xFFFF))) {
+                    if (ls == 0) {
+                        ext_out r;
+                        r.score = 0; r.a = 0; r.b = 0; r.carry = 0u; r.cells = 0;
+                        out[x.task] = r;
+                    }
+                    continue;
+                }
+                const int64_t qo = qoffsets[c.i], to = toffsets[c.j];
+                const int lq = (int)(qoffsets[c.i + 1] - qo), lt = (int)(toffsets[c.j + 1] - to);
+                const int pi = c.qpos[seed], pj = c.tpos[seed];
+                const int A = left ? pi : lq - pi - k, B = left ? pj : lt - pj - k;
+                if (A < 1 || B < 1 || smax * min(A, B) > XD16_LIM) {
+                    if (ls == 0) ovf_list[atomicAdd(ovf_n, 1u)] = (uint32_t)x.task;
+                    continue;
+                }
+                x.q = left ? qcodes + qo + pi - 1 : qcodes + qo + pi + k;
+                x.t = left ? tcodes + to + pj - 1 : tcodes + to + pj + k;
+                x.A = A; x.B = B; x.st = left ? -1 : 1;
+                // antidiagonal 0: the anchor, diagonal 0 = the low half of lane 64 / 4R's
+                // first even register
+                x.kbase = -64;
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        x.H[pp][r] = XD16_NEG2; x.E[pp][r] = XD16_NEG2; x.F[pp][r] = XD16_NEG2;
+                    }
+                if (ls == 64 / WD) x.H[0][0] = XD16_NEG2 & 0xffff0000u;
+                x.d = 0; x.best = 0; x.sd = 0; x.sa0 = 0; x.llo = 0; x.lhi = 0; x.cells = 1;
+                xd16_load_windows(x, 0, (x.kbase + WD * ls) >> 1, lane4);
+                x.active = true;
+            }
+        }
+        if (__all_sync(0xffffffffu, exhausted)) break;
+        xd16_step<R, 1>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
+        xd16_step<R, 0>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
+    }
+}
+
 // Extension tasks: task = 4 p + 2 seed + left.  With a task list the kernel runs only
 // the listed tasks (*d_ntask of them): the second phase of the filter-only mode.
 template <bool CARRY>
@@ -487,7 +805,8 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     int8_t *dmat;
     PASTIS_WS(dmat, ctx, WS_FLAGS, 1024);
     int *flags = (int *)(dmat + 768);   // [0] error, [1] [3] [8] pair counters, [2] max length, [4] bad pair,
-                                        // [5] bad code, [6..7] task counter
+                                        // [5] bad code, [6..7] [12..13] [14..15] task counters, [9] the
+                                        // 16-bit x-drop's deferred tasks
     // the matrix, then the pass-1 layout at dmat + 640
     uint8_t hconst[640 + PASTIS_SW_BINS];
     memcpy(hconst, params->matrix, 576);
@@ -575,13 +894,50 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
             uint32_t *need;
             PASTIS_WS(need, ctx, WS_ALN_ORDER, sizeof(uint32_t) * (3 * (size_t)n4 + 4));
             uint32_t *off = need + n4, *list = off + n4 + 1;
-            prof_begin(ctx, "xd_extend");
-            k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
-                                                            n_pairs, params->k, dmat, params->gap_open,
-                                                            params->gap_extend, params->xdrop, gbuf, W, flags + 6,
-                                                            ext, nullptr, nullptr, dn, chk);
-            PASTIS_LAUNCHED(ctx);
-            prof_end(ctx);
+            const int per_warp = ctx->xd_per_warp;
+            if (per_warp && xd16_params_fit(params->gap_open, params->gap_extend, params->xdrop)) {
+                // in 16-bit lanes, per_warp extensions per warp; the tasks it cannot hold
+                // are listed (list[flags[9]]) and run in 32-bit lanes
+                int smax = -64;
+                for (int x = 0; x < PASTIS_NSYM * PASTIS_NSYM; ++x) smax = std::max(smax, (int)params->matrix[x]);
+                uint32_t *ovf_n = (uint32_t *)(flags + 9);
+                int per_sm = 1;
+                prof_begin(ctx, "xd_extend");
+                if (per_warp == 1) {
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<1>, ALN_THREADS, 0);
+                    k_xd_ext16<1><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, st>>>(
+                        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
+                        params->gap_open, params->gap_extend, params->xdrop, smax, flags + 14, ext, list, ovf_n, dn,
+                        chk);
+                } else if (per_warp == 2) {
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<2>, ALN_THREADS, 0);
+                    k_xd_ext16<2><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, st>>>(
+                        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
+                        params->gap_open, params->gap_extend, params->xdrop, smax, flags + 14, ext, list, ovf_n, dn,
+                        chk);
+                } else {
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<4>, ALN_THREADS, 0);
+                    k_xd_ext16<4><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, st>>>(
+                        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
+                        params->gap_open, params->gap_extend, params->xdrop, smax, flags + 14, ext, list, ovf_n, dn,
+                        chk);
+                }
+                PASTIS_LAUNCHED(ctx);
+                k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                                n_pairs, params->k, dmat, params->gap_open,
+                                                                params->gap_extend, params->xdrop, gbuf, W, flags + 6,
+                                                                ext, list, ovf_n, dn, chk);
+                PASTIS_LAUNCHED(ctx);
+                prof_end(ctx);
+            } else {
+                prof_begin(ctx, "xd_extend");
+                k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                                n_pairs, params->k, dmat, params->gap_open,
+                                                                params->gap_extend, params->xdrop, gbuf, W, flags + 6,
+                                                                ext, nullptr, nullptr, dn, chk);
+                PASTIS_LAUNCHED(ctx);
+                prof_end(ctx);
+            }
             k_xd_mark<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_qoffsets, d_toffsets, d_pairs, n_pairs,
                                                                           params->k, params->cov_min_pct, ext, need,
                                                                           dn, chk);
@@ -638,6 +994,14 @@ extern "C" pastis_status pastis_sw_layout_set(pastis_ctx *ctx, const uint8_t *h_
     ctx->sw_lay = lay;
     return PASTIS_OK;
 }
+
+extern "C" pastis_status pastis_xd_layout_set(pastis_ctx *ctx, int32_t per_warp) {
+    if (!ctx || (per_warp != 0 && per_warp != 1 && per_warp != 2 && per_warp != 4)) return PASTIS_ERR_INVALID_ARG;
+    ctx->xd_per_warp = per_warp;
+    return PASTIS_OK;
+}
+
+extern "C" int32_t pastis_xd_layout_get(const pastis_ctx *ctx) { return ctx ? ctx->xd_per_warp : -1; }
 
 extern "C" pastis_status pastis_sw_layout_get(const pastis_ctx *ctx, uint8_t *h_extra) {
     if (!ctx || !h_extra) return PASTIS_ERR_INVALID_ARG;
@@ -699,6 +1063,66 @@ extern "C" pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qc
         for (int b = 0; b < PASTIS_SW_BINS; ++b) h_extra[b] = best.extra[b];
     if (h_cycles)
         for (int x = 0; x < NX * PASTIS_SW_BINS; ++x) h_cycles[x] = cyc[x];
+    return PASTIS_OK;
+}
+
+// The x-drop lane layout: the filter-only x-drop of the pairs under each setting (32-bit
+// lanes, then 1, 2 and 4 extensions per warp in 16-bit lanes), each call timed by CUDA
+// events on the context's stream, the best of `reps`; the fastest setting when it beats
+// the current one by 2% or more, else the current one.
+extern "C" pastis_status pastis_autotune_xd(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets,
+                                            int32_t n_q, const uint8_t *d_tcodes, const int64_t *d_toffsets,
+                                            int32_t n_t, const pastis_cand *d_pairs, int64_t n_pairs,
+                                            const pastis_params *params, int32_t reps, int32_t *h_per_warp,
+                                            double *h_ms) {
+    if (!ctx || !params || reps < 1 || n_pairs < 0) return PASTIS_ERR_INVALID_ARG;
+    pastis_status s = check_params(params);
+    if (s != PASTIS_OK) return s;
+    if (params->mode != PASTIS_XD && params->mode != PASTIS_XD_FILTERED) return PASTIS_ERR_UNSUPPORTED;
+    constexpr int NX = 4;
+    const int choice[NX] = {0, 1, 2, 4};
+    const int saved = ctx->xd_per_warp;
+    double ms[NX] = {0.0, 0.0, 0.0, 0.0};
+    if (n_pairs > 0) {
+        pastis_aln *d_out;
+        PASTIS_WS(d_out, ctx, WS_TUNE, sizeof(pastis_aln) * (size_t)n_pairs + 16);
+        pastis_params ps = *params;
+        ps.mode = PASTIS_XD_FILTERED;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+            cudaGetLastError();
+            if (ev[0]) cudaEventDestroy(ev[0]);
+            return PASTIS_ERR_CUDA;
+        }
+        for (int r = 0; r < reps && s == PASTIS_OK; ++r) {
+            for (int x = 0; x < NX && s == PASTIS_OK; ++x) {
+                ctx->xd_per_warp = choice[x];
+                if (cudaEventRecord(ev[0], ctx->stream) != cudaSuccess) { s = PASTIS_ERR_CUDA; break; }
+                s = align_qt(ctx, d_qcodes, d_qoffsets, n_q, d_tcodes, d_toffsets, n_t, d_pairs, n_pairs, &ps, d_out,
+                             nullptr);
+                float t = 0.f;
+                if (s == PASTIS_OK && (cudaEventRecord(ev[1], ctx->stream) != cudaSuccess ||
+                                       cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                                       cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess))
+                    s = PASTIS_ERR_CUDA;
+                if (s == PASTIS_OK && (r == 0 || t < ms[x])) ms[x] = t;
+            }
+        }
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        ctx->xd_per_warp = saved;
+        if (s != PASTIS_OK) { cudaGetLastError(); return s; }
+        int cur = 0, bx = 0;
+        for (int x = 0; x < NX; ++x) {
+            if (choice[x] == saved) cur = x;
+            if (ms[x] < ms[bx]) bx = x;
+        }
+        if (ms[bx] > 0.98 * ms[cur]) bx = cur;
+        ctx->xd_per_warp = choice[bx];
+    }
+    if (h_per_warp) *h_per_warp = ctx->xd_per_warp;
+    if (h_ms)
+        for (int x = 0; x < NX; ++x) h_ms[x] = ms[x];
     return PASTIS_OK;
 }
 

@@ -42,6 +42,7 @@ extern "C" pastis_status pastis_ctx_create(pastis_ctx **ctx, int device, void *s
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { free(c); return PASTIS_ERR_CUDA; }
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
+    c->xd_per_warp = PASTIS_XD_DEFAULT_PER_WARP;
     // Kernels with a per-call dynamic shared-memory size get the device's limit once
     // here; a per-call setting could lower it under a launch of another thread.
     if (sw_set_smem_limit(c->smem_optin) != cudaSuccess || spgemm_set_smem_limit(c->smem_optin) != cudaSuccess) {

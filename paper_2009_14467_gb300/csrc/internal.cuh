@@ -81,6 +81,7 @@ struct pastis_ctx {
     int prof_on;
     unsigned long long *d_stats;   // work counters while profiling: see pastis_ctx_stats
     sw_layout sw_lay;              // pass-1 stripe layout per query-length bin
+    int xd_per_warp;               // x-drop extensions per warp in 16-bit lanes (1, 2, 4); 0 = 32-bit lanes
     unsigned long long *d_tune;    // per-bin pass-1 cycles while the tuner runs, else null
     int prof_open;
     int prof_n;

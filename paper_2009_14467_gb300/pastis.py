@@ -19,6 +19,7 @@ ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 SW, XD, SW_SCORE, SW_FILTERED, XD_FILTERED = 0, 1, 2, 3, 4
 SW_BINS, SW_BIN_WIDTH, SW_MAX_EXTRA = 64, 32, 2     # pass-1 layout per query-length bin
 SW_INT32 = 3                                        # a layout value: the bin's pairs in 32-bit lanes
+XD_DEFAULT_PER_WARP = 4                             # x-drop extensions per warp in 16-bit lanes
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_RESIDUE", 3: "CAPACITY", 4: "OUT_OF_MEMORY",
           5: "CUDA", 6: "TIMEOUT", 7: "UNSUPPORTED", 8: "INTERNAL"}
@@ -214,6 +215,16 @@ class Context:
             raise ValueError(f"a layout has {SW_BINS} entries")
         _check("pastis_sw_layout_set", lib().pastis_sw_layout_set(self.h, a.ctypes.data_as(ctypes.c_void_p)))
 
+    def xd_layout(self) -> int:
+        """pastis_xd_layout_get: x-drop extensions per warp in 16-bit lanes (0: 32-bit lanes)."""
+        _layout_sigs()
+        return int(lib().pastis_xd_layout_get(self.h))
+
+    def set_xd_layout(self, per_warp: int = XD_DEFAULT_PER_WARP):
+        """pastis_xd_layout_set: 1, 2 or 4 extensions per warp in 16-bit lanes, 0 for 32-bit lanes."""
+        _layout_sigs()
+        _check("pastis_xd_layout_set", lib().pastis_xd_layout_set(self.h, int(per_warp)))
+
 
 @dataclass
 class KMat:
@@ -327,6 +338,12 @@ def _layout_sigs():
         L.pastis_sw_layout_set.restype = i32
         L.pastis_sw_layout_get.argtypes = [P, P]
         L.pastis_sw_layout_get.restype = i32
+        L.pastis_xd_layout_set.argtypes = [P, i32]
+        L.pastis_xd_layout_set.restype = i32
+        L.pastis_xd_layout_get.argtypes = [P]
+        L.pastis_xd_layout_get.restype = i32
+        L.pastis_autotune_xd.argtypes = [P, P, P, i32, P, P, i32, P, i64, ctypes.POINTER(c_params), i32, P, P]
+        L.pastis_autotune_xd.restype = i32
         L.pastis_autotune_sw.argtypes = [P, P, P, i32, P, P, i32, P, i64, ctypes.POINTER(c_params), i32, P, P]
         L.pastis_autotune_sw.restype = i32
         L._layout_sigs = True
@@ -350,6 +367,26 @@ def autotune_sw(ctx: Context, codes: torch.Tensor, offsets: torch.Tensor, pairs:
                                                       extra.ctypes.data_as(ctypes.c_void_p),
                                                       cyc.ctypes.data_as(ctypes.c_void_p)))
     return extra, cyc
+
+
+XD_CHOICES = (0, 1, 2, 4)
+
+
+def autotune_xd(ctx: Context, codes: torch.Tensor, offsets: torch.Tensor, pairs: torch.Tensor, params: Params,
+                reps: int = 2, tcodes: torch.Tensor = None, toffsets: torch.Tensor = None):
+    """pastis_autotune_xd over the given pairs.  Sets the chosen x-drop layout on ctx and
+    returns (per_warp, {setting: best ms}) for the settings 0, 1, 2, 4."""
+    L = _layout_sigs()
+    tcodes = codes if tcodes is None else tcodes
+    toffsets = offsets if toffsets is None else toffsets
+    pw = ctypes.c_int32()
+    ms = (ctypes.c_double * 4)()
+    p = params.c()
+    _check("pastis_autotune_xd", L.pastis_autotune_xd(ctx.h, _ptr(codes), _ptr(offsets), offsets.numel() - 1,
+                                                      _ptr(tcodes), _ptr(toffsets), toffsets.numel() - 1,
+                                                      _ptr(pairs), pairs.shape[0], ctypes.byref(p), reps,
+                                                      ctypes.byref(pw), ms))
+    return pw.value, {c: ms[x] for x, c in enumerate(XD_CHOICES)}
 
 
 def _plan_sigs():

@@ -1,6 +1,7 @@
 """The Smith-Waterman pass-1 layout (extra stripes, or 32-bit lanes, per query-length bin)
 and its autotuner: every layout gives the same records as the default and the oracle, the
-tuner returns and sets a valid layout, and bad layouts or modes are refused."""
+tuner returns and sets a valid layout, and bad layouts or modes are refused.  The same
+for the x-drop lane layout's tuner (extensions per warp in 16-bit lanes)."""
 import numpy as np
 import pytest
 import torch
@@ -122,3 +123,26 @@ def test_bad_layouts_and_modes_are_refused(env):
     assert np.array_equal(ctx.sw_layout(), LAYOUTS["one"])
     ctx.set_sw_layout(None)
     assert (ctx.sw_layout() == 0).all()
+
+
+def test_xd_autotune_sets_a_valid_setting(env):
+    """The x-drop lane tuner: times every setting, sets the fastest (or keeps the current
+    one within 2%), and the tuned context still gives the oracle's mode-4 records."""
+    P, ctx = env
+    ps, codes, c = _families()
+    params = P.Params(matrix=MAT, mode=P.XD_FILTERED)
+    ctx.set_xd_layout()
+    pw, ms = P.autotune_xd(ctx, dev(codes), dev(ps.offsets), recs(c), params, reps=2)
+    assert pw in P.XD_CHOICES and ctx.xd_layout() == pw
+    assert set(ms) == set(P.XD_CHOICES) and all(v > 0 for v in ms.values())
+    if pw != P.XD_DEFAULT_PER_WARP:
+        assert ms[pw] == min(ms.values()) and ms[pw] <= 0.98 * ms[P.XD_DEFAULT_PER_WARP]
+    got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets), recs(c), params), P.ALN_DTYPE)
+    want, _ = O.align_pairs(codes, ps.offsets, c, MAT, mode=P.XD_FILTERED)
+    assert got.tobytes() == want.tobytes()
+    # the SW modes are refused and the setting stays
+    with pytest.raises(P.PastisError) as e:
+        P.autotune_xd(ctx, dev(codes), dev(ps.offsets), recs(c[:100]), P.Params(matrix=MAT, mode=P.SW))
+    assert e.value.status == 7
+    assert ctx.xd_layout() == pw
+    ctx.set_xd_layout()

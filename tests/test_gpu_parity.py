@@ -404,3 +404,59 @@ def test_xd_filtered_substitute_seeds(P, ctx):
     got, want, gc, wc = _align_both(P, ctx, ps, cands, P.XD_FILTERED)
     assert gc == wc
     _cmp_alns(got, want)
+
+
+def _xd_mat(scale):
+    m = MAT.astype(np.int32) * scale
+    return np.clip(m, -64, 63).astype(np.int8)
+
+
+@pytest.mark.parametrize("per_warp", [0, 1, 2, 4])
+@pytest.mark.parametrize("which", ["families", "wide", "edge_cases", "big_scores"])
+def test_xd_lanes_parity(P, ctx, per_warp, which):
+    """The filter-only x-drop's first phase in 16-bit lanes (1, 2 or 4 extensions per
+    warp) or in 32-bit lanes: every field against the oracle's mode 4.  'wide' (X = 1000)
+    grows computed antidiagonals past the 16-bit window, 'edge_cases' has seeds at
+    sequence ends (sides of length 0) and short sequences, 'big_scores' a matrix whose
+    scores times the extension length pass the 16-bit bound: those extensions run in
+    32-bit lanes, with identical results."""
+    mat, kw = MAT, {}
+    if which == "edge_cases":
+        ps = edge_case_set()
+        cands = _cands(P, ctx, ps, k=2)[1]
+        kw["k"] = 2
+    elif which == "big_scores":
+        ps = synth.families_1k().subset(np.arange(300))
+        cands = _cands(P, ctx, ps)[1]
+        mat = _xd_mat(6)
+    else:
+        ps = synth.families_1k()
+        cands = _cands(P, ctx, ps)[1]
+        if which == "wide":
+            kw["xdrop"] = 1000
+    assert len(cands) > 0
+    codes = O.encode(ps.ascii)
+    params = P.Params(matrix=mat, mode=P.XD_FILTERED, **kw)
+    ctx.set_xd_layout(per_warp)
+    try:
+        cells = torch.zeros(1, dtype=torch.int64, device="cuda")
+        got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets),
+                                         dev(cands.view(np.uint8).reshape(-1, 20)), params, cells), P.ALN_DTYPE)
+    finally:
+        ctx.set_xd_layout()
+    want, wcells = O.align_pairs(codes, ps.offsets, cands, mat, params.gap_open, params.gap_extend, P.XD_FILTERED,
+                                 params.xdrop, params.k, params.ani_min_pct, params.cov_min_pct)
+    _cmp_alns(got, want)
+    assert int(cells.item()) == wcells
+
+
+def test_xd_layout_setting(P, ctx):
+    assert ctx.xd_layout() == P.XD_DEFAULT_PER_WARP
+    for bad in (-1, 3, 5, 8, 32):
+        with pytest.raises(RuntimeError):
+            ctx.set_xd_layout(bad)
+        assert ctx.xd_layout() == P.XD_DEFAULT_PER_WARP
+    for ok in (0, 1, 2, 4):
+        ctx.set_xd_layout(ok)
+        assert ctx.xd_layout() == ok
+    ctx.set_xd_layout()
