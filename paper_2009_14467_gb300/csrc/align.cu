@@ -344,7 +344,15 @@ constexpr uint32_t XD16_QOFF = PASTIS_NSYM / 2 * 128;      // bytes per query re
 // Whether the 16-bit kernel may run an x-drop with these penalties at all.
 static inline bool xd16_params_fit(int o, int e, int X) { return o <= 128 && e <= 128 && X <= XD16_LIM; }
 
-__device__ __forceinline__ uint32_t xd16_pk(int v) { return (uint32_t)(v & 0xffff) * 0x10001u; }
+__device__ __forceinline__ uint32_t xd16_pk(int v) { return __byte_perm((uint32_t)v, 0u, 0x1010); }
+
+// Live bits of four cells in row order from the dead masks of two registers (halves of
+// 0xffff or 0): the high byte of each half, gathered in row order, then its top bit
+// moved to bit j by one multiply (the partial products below bit 28 never carry into it).
+__device__ __forceinline__ uint32_t xd16_live4(uint32_t dm0, uint32_t dm1) {
+    const uint32_t x = ~__byte_perm(dm0, dm1, 0x7531) & 0x80808080u;
+    return (x * 0x00204081u) >> 28;
+}
 
 template <int R>
 struct xd16_ext {
@@ -434,7 +442,7 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
         }
     }
     const int lim = x.best - X;
-    const uint32_t lim2 = xd16_pk(lim), limm2 = xd16_pk(lim - 1);
+    const uint32_t lim2 = xd16_pk(lim), limm2 = __vsub2(lim2, 0x00010001u);
     const uint32_t span2 = xd16_pk(chi - clo), rb2 = xd16_pk(a0 - clo);
     // the sources on d - 1 that cross a lane boundary
     uint32_t bh, bx;
@@ -447,7 +455,7 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
         bx = __shfl_down_sync(0xffffffffu, x.E[Q][0], 1, G);
         if (ls == G - 1) { bh = XD16_NEG2; bx = XD16_NEG2; }
     }
-    uint32_t lbw = 0u;                           // live cells: bit r = cell 2r, bit 16 + r = cell 2r + 1
+    uint32_t dmk[R];                             // dead masks, for the live bits below
     uint32_t hmax = XD16_NEG2;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -476,12 +484,21 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
         x.H[P][r] = (hn & ~dm) | (XD16_NEG2 & dm);
         x.E[P][r] = (en & ~dm) | (XD16_NEG2 & dm);
         x.F[P][r] = (fn & ~dm) | (XD16_NEG2 & dm);
-        lbw |= (~dm & 0x00010001u) << r;
+        dmk[r] = dm;
         hmax = __vmaxs2(hmax, x.H[P][r]);
+    }
+    // live cells of this lane, bit j = row a0 + j
+    uint32_t lb;
+    if (R == 1) {
+        const uint32_t y = ~dmk[0] & 0x80008000u;
+        lb = ((y >> 15) & 1u) | (y >> 30);
+    } else {
+        lb = xd16_live4(dmk[0], dmk[R > 1 ? 1 : 0]);
+        if (R == 4) lb |= xd16_live4(dmk[R > 2 ? 2 : 0], dmk[R > 3 ? 3 : 0]) << 4;
     }
     x.cells += empty ? 0 : chi - clo + 1;
     x.d = d;
-    const unsigned bal = (__ballot_sync(0xffffffffu, lbw != 0u) >> sbase) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
+    const unsigned bal = (__ballot_sync(0xffffffffu, lb != 0u) >> sbase) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
     const int myh = max((int)(short)(hmax & 0xffffu), (int)hmax >> 16);
     const int toph = __reduce_max_sync(smask, myh);
     const bool raise = !empty && !defer && toph > x.best;
@@ -490,12 +507,9 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
     x.sa0 = raise ? a0 : x.sa0;
     x.sd = raise ? d : x.sd;
     x.best = raise ? toph : x.best;
-    const uint32_t lo_b = lbw & 0xffffu, hi_b = lbw >> 16;
-    const int jlo = min(lo_b ? 2 * (__ffs(lo_b) - 1) : NC, hi_b ? 2 * (__ffs(hi_b) - 1) + 1 : NC);
-    const int jhi = max(lo_b ? 2 * (31 - __clz(lo_b)) : -1, hi_b ? 2 * (31 - __clz(hi_b)) + 1 : -1);
     const int first = __ffs(bal) - 1, last = 31 - __clz(bal);
-    x.llo = __shfl_sync(0xffffffffu, a0 + jlo, first & (G - 1), G);
-    x.lhi = __shfl_sync(0xffffffffu, a0 + jhi, last & (G - 1), G);
+    x.llo = __shfl_sync(0xffffffffu, a0 + __ffs(lb) - 1, first & (G - 1), G);
+    x.lhi = __shfl_sync(0xffffffffu, a0 + 31 - __clz(lb), last & (G - 1), G);
     // the end of the extension, or its hand-over to the 32-bit kernel
     const bool stop = x.active && (defer || empty || bal == 0u);
     if (__any_sync(0xffffffffu, stop)) {
