@@ -385,7 +385,7 @@ pastis_status pastis_autotune_xd(pastis_ctx *ctx, const uint8_t *d_qcodes, const
  * equals pastis_align_pairs_qt's on the same batch.
  *
  * pastis_align_plan_create: ctx supplies the device, the stream (the plan runs on it)
- *   and the pass-1 layout at this moment; the plan owns a private workspace.  Targets
+ *   and the pass-1 and x-drop layouts at this moment; the plan owns a private workspace.  Targets
  *   d_tcodes / d_toffsets[n_t+1] (device; they must stay valid and unchanged while the
  *   plan lives) are checked once: a code >= 24 gives PASTIS_ERR_INVALID_RESIDUE, a
  *   target longer than max_len PASTIS_ERR_INVALID_ARG.  Capacities: max_q queries,

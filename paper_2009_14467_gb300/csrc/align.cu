@@ -1229,6 +1229,7 @@ extern "C" pastis_status pastis_align_plan_create(pastis_ctx *ctx, const uint8_t
     s = pastis_ctx_create(&p->ctx, ctx->device, (void *)st);
     if (s != PASTIS_OK) { plan_free(p); return s; }
     p->ctx->sw_lay = ctx->sw_lay;
+    p->ctx->xd_per_warp = ctx->xd_per_warp;
 #define PLAN_TRY(expr) do { if ((expr) != cudaSuccess) { cudaGetLastError(); plan_free(p); return PASTIS_ERR_OUT_OF_MEMORY; } } while (0)
     PLAN_TRY(cudaMalloc(&p->qcodes, (size_t)max_qres + 16));
     PLAN_TRY(cudaMalloc(&p->qoffsets, sizeof(int64_t) * ((size_t)max_q + 1)));
