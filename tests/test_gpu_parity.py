@@ -450,6 +450,31 @@ def test_xd_lanes_parity(P, ctx, per_warp, which):
     assert int(cells.item()) == wcells
 
 
+@pytest.mark.parametrize("o,e,X", [(128, 1, 49), (129, 1, 49), (11, 1, 30000), (11, 1, 30001), (3, 1, 49),
+                                   (1, 1, 5), (40, 30, 49)])
+def test_xd_lanes_bounds(P, ctx, o, e, X):
+    """At and past the 16-bit kernel's bounds (gap open or extend 128 vs 129, X 30,000 vs
+    30,001) and with cheap or costly gaps (wide or narrow bands), every field of the
+    filter-only x-drop equals the oracle's, in 16-bit lanes (four per warp) and in 32-bit
+    lanes."""
+    ps = synth.families_1k().subset(np.arange(400))
+    cands = _cands(P, ctx, ps)[1]
+    codes = O.encode(ps.ascii)
+    params = P.Params(matrix=MAT, mode=P.XD_FILTERED, gap_open=o, gap_extend=e, xdrop=X)
+    want, wcells = O.align_pairs(codes, ps.offsets, cands, MAT, o, e, P.XD_FILTERED, X, params.k,
+                                 params.ani_min_pct, params.cov_min_pct)
+    for pw in (4, 0):
+        ctx.set_xd_layout(pw)
+        try:
+            cells = torch.zeros(1, dtype=torch.int64, device="cuda")
+            got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets),
+                                             dev(cands.view(np.uint8).reshape(-1, 20)), params, cells), P.ALN_DTYPE)
+        finally:
+            ctx.set_xd_layout()
+        _cmp_alns(got, want)
+        assert int(cells.item()) == wcells
+
+
 def test_xd_layout_setting(P, ctx):
     assert ctx.xd_layout() == P.XD_DEFAULT_PER_WARP
     for bad in (-1, 3, 5, 8, 32):
