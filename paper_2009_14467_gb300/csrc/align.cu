@@ -500,7 +500,11 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
     x.d = d;
     const unsigned bal = (__ballot_sync(0xffffffffu, lb != 0u) >> sbase) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
     const int myh = max((int)(short)(hmax & 0xffffu), (int)hmax >> 16);
-    const int toph = __reduce_max_sync(smask, myh);
+    // the segment's maximum by a butterfly of full-warp shuffles (a reduction with a
+    // per-segment member mask runs once per distinct mask)
+    int toph = myh;
+#pragma unroll
+    for (int m = G / 2; m > 0; m >>= 1) toph = max(toph, __shfl_xor_sync(0xffffffffu, toph, m, G));
     const bool raise = !empty && !defer && toph > x.best;
 #pragma unroll
     for (int r = 0; r < R; ++r) x.HS[r] = raise ? x.H[P][r] : x.HS[r];
