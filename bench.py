@@ -905,11 +905,24 @@ def main():
         qi = cands.view(torch.int32).view(-1, 5)[:, 0]
         sample = cands[(qi % stride) == 0].contiguous()
         pw, tms = P.autotune_xd(ctx, codes, offs_dev, sample, params, reps=2)
+        # the same timings per query-length bin of the sample (the setting is one per
+        # batch; this shows whether any bin would choose otherwise)
+        label = lambda c: "32-bit lanes" if c == 0 else f"16-bit lanes, {c} per warp"
+        qlen = np.diff(ps.offsets)[sample.view(torch.int32).view(-1, 5)[:, 0].cpu().numpy()]
+        by_bin = {}
+        for lo, hi in ((50, 150), (150, 300), (300, 600), (600, 2001)):
+            sel = torch.from_numpy(np.flatnonzero((qlen >= lo) & (qlen < hi))).to(dev)
+            if sel.numel() == 0:
+                continue
+            bpw, bms = P.autotune_xd(ctx, codes, offs_dev, sample[sel].contiguous(), params, reps=2)
+            by_bin[f"{lo}-{hi - 1}"] = {"pairs": int(sel.numel()), "fastest": label(min(bms, key=bms.get)),
+                                        "ms": {label(c): round(v, 3) for c, v in bms.items()}}
+        ctx.set_xd_layout(pw)
         torch.cuda.synchronize()
         tune = {"sample_pairs": int(sample.shape[0]), "sample": f"candidates of every {stride}th query of block 0",
                 "setup_s": round(time.perf_counter() - t0, 2), "xd_per_warp": pw,
-                "xd_ms_by_setting": {("32-bit lanes" if c == 0 else f"16-bit lanes, {c} per warp"): round(v, 3)
-                                     for c, v in tms.items()}}
+                "xd_ms_by_setting": {label(c): round(v, 3) for c, v in tms.items()},
+                "by_query_length": by_bin}
         del codes, A, cands, qi, sample
 
     # the integer-pipe peak, measured on this GPU (warp-instructions per SM clock of each
