@@ -1051,6 +1051,14 @@ def main():
                     "traffic": None, "kernel": "spgemm (cursors, rows, concat)", "peak_source": src,
                     "products": stats["spgemm_products"], "left_entries": stats["spgemm_left_entries"],
                     "records": stats["spgemm_records"]}
+        # the same with the sorts that build A and AS counted as well: 8 bytes per element
+        # per 8-bit digit pass, and the radix kernels' time
+        sort_ms = sum(v[1] for k, v in prof.items() if k.startswith("radix"))
+        if sort_ms > 0 and stats["sort_element_passes"] > 0:
+            b2 = spg_bytes + 8 * stats["sort_element_passes"]
+            a2 = b2 / ((spg_ms + sort_ms) / 1000.0) / 1e9
+            roof_spg["with_sorts"] = {"achieved": a2, "frac": a2 / peak_gbs, "sort_element_passes":
+                                      stats["sort_element_passes"], "sort_ms": sort_ms, "spgemm_ms": spg_ms}
     sw_block = None
     if w["mode"] in (1, 4) and rank == 0:
         # full SW over one block's candidates (the sample of the x-drop workload's pairs)

@@ -171,7 +171,9 @@ int32_t pastis_ctx_profile_read(pastis_ctx *ctx, char *buf, int32_t len);
 /* Work counters accumulated while profiling is on (cleared when it is enabled), for the
  * roofline of the overlap product: h_out[0] = posting entries visited (products),
  * [1] = left-operand entries of the rows formed (each once per row), [2] = candidate
- * records written.  Entries past the third are 0.  Synchronises the stream.                 */
+ * records written, [3] = radix-sort element passes of the k-mer matrix builds (A and AS:
+ * elements sorted x 8-bit digit passes).  Entries past the fourth are 0.  Synchronises
+ * the stream.                                                                             */
 #define PASTIS_STATS 4
 pastis_status pastis_ctx_stats(pastis_ctx *ctx, int64_t *h_out, int32_t n);
 

@@ -45,7 +45,8 @@ extern "C" pastis_status pastis_ctx_create(pastis_ctx **ctx, int device, void *s
     c->xd_per_warp = PASTIS_XD_DEFAULT_PER_WARP;
     // Kernels with a per-call dynamic shared-memory size get the device's limit once
     // here; a per-call setting could lower it under a launch of another thread.
-    if (sw_set_smem_limit(c->smem_optin) != cudaSuccess || spgemm_set_smem_limit(c->smem_optin) != cudaSuccess) {
+    if (sw_set_smem_limit(c->smem_optin) != cudaSuccess || spgemm_set_smem_limit(c->smem_optin) != cudaSuccess ||
+        radix_set_smem_limit() != cudaSuccess) {
         cudaGetLastError();
         free(c);
         return PASTIS_ERR_CUDA;
@@ -104,6 +105,7 @@ extern "C" pastis_status pastis_ctx_profile(pastis_ctx *ctx, int enable) {
             return PASTIS_ERR_OUT_OF_MEMORY;
         }
         PASTIS_CUDA_TRY(cudaMemsetAsync(ctx->d_stats, 0, PASTIS_STATS * sizeof(unsigned long long), ctx->stream));
+        ctx->sort_passes = 0;
     }
     ctx->prof_on = enable ? 1 : 0;
     ctx->prof_open = 0;
@@ -117,6 +119,7 @@ extern "C" pastis_status pastis_ctx_stats(pastis_ctx *ctx, int64_t *h_out, int32
         PASTIS_CUDA_TRY(cudaMemcpyAsync(v, ctx->d_stats, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
         PASTIS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     }
+    v[3] = (unsigned long long)ctx->sort_passes;
     for (int x = 0; x < n; ++x) h_out[x] = x < PASTIS_STATS ? (int64_t)v[x] : 0;
     return PASTIS_OK;
 }

@@ -80,6 +80,7 @@ struct pastis_ctx {
     // profiling: pending event pairs and per-name totals
     int prof_on;
     unsigned long long *d_stats;   // work counters while profiling: see pastis_ctx_stats
+    int64_t sort_passes;           // radix-sort element passes while profiling (pastis_ctx_stats [3])
     sw_layout sw_lay;              // pass-1 stripe layout per query-length bin
     int xd_per_warp;               // x-drop extensions per warp in 16-bit lanes (1, 2, 4); 0 = 32-bit lanes
     unsigned long long *d_tune;    // per-bin pass-1 cycles while the tuner runs, else null
@@ -142,6 +143,7 @@ pastis_status exclusive_scan_i64(pastis_ctx *c, const int64_t *in, int64_t *out,
 // device's opt-in maximum (the current device; done at context creation).
 cudaError_t sw_set_smem_limit(size_t bytes);
 cudaError_t spgemm_set_smem_limit(size_t bytes);
+cudaError_t radix_set_smem_limit();
 
 // Validates the parameters shared by the calls; returns PASTIS_OK or INVALID_ARG.
 pastis_status check_params(const pastis_params *p);

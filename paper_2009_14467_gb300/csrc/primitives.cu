@@ -154,15 +154,28 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *keys, in
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = s_h[threadIdx.x];
 }
 
+// The tile's items are first placed in shared memory in their sorted order (digit, then
+// input order), then written out in that order, so consecutive threads write
+// consecutive positions of each digit's run in the output.
+constexpr size_t RS_SCATTER_SMEM = sizeof(uint64_t) * RS_TILE + sizeof(uint32_t) * RS_TILE +
+                                   sizeof(uint32_t) * (2 * RS_WARPS * 256 + 2 * 256 + RS_WARPS);
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *keys, const uint64_t *vals,
                                                            int64_t n, int shift, const uint32_t *offs,
                                                            int64_t nb, uint32_t *okeys, uint64_t *ovals) {
-    __shared__ uint32_t s_cnt[RS_WARPS][256];
-    __shared__ uint32_t s_base[RS_WARPS][256];
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t *s_v = reinterpret_cast<uint64_t *>(rs_smem);
+    uint32_t *s_k = reinterpret_cast<uint32_t *>(s_v + RS_TILE);
+    uint32_t *s_cnt = s_k + RS_TILE;                 // [warp][digit]: counts, then ranks so far
+    uint32_t *s_base = s_cnt + RS_WARPS * 256;       // [warp][digit]: start within the digit's run
+    uint32_t *s_tstart = s_base + RS_WARPS * 256;    // [digit]: start of the digit's run in the tile
+    uint32_t *s_gbase = s_tstart + 256;              // [digit]: its start in the output
+    uint32_t *s_wsum = s_gbase + 256;                // [warp]: scan carries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < 256 * RS_WARPS; d += RS_THREADS) (&s_cnt[0][0])[d] = 0;
+    for (int d = threadIdx.x; d < 256 * RS_WARPS; d += RS_THREADS) s_cnt[d] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_ITEMS * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = tile0 + (int64_t)warp * (RS_ITEMS * 32);
     uint32_t k[RS_ITEMS];
     uint64_t v[RS_ITEMS];
     uint32_t dg[RS_ITEMS];
@@ -178,36 +191,58 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *keys,
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; ++it) {
         unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
-        if (dg[it] < 256u && lane == __ffs(peers) - 1) s_cnt[warp][dg[it]] += __popc(peers);
+        if (dg[it] < 256u && lane == __ffs(peers) - 1) s_cnt[warp * 256 + dg[it]] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    {
-        int d = threadIdx.x;   // RS_THREADS == 256 digits
-        uint32_t run = offs[(int64_t)d * nb + blockIdx.x];
-        for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t cnt = s_cnt[w][d];
-            s_base[w][d] = run;
-            run += cnt;
-            s_cnt[w][d] = 0;
-        }
+    // per digit: the warps' starts within its run, its total, and the runs' starts in the
+    // tile (an exclusive scan over the digits)
+    const int d0 = threadIdx.x;                      // RS_THREADS == 256 digits
+    uint32_t tot = 0;
+    for (int w = 0; w < RS_WARPS; ++w) {
+        s_base[w * 256 + d0] = tot;
+        tot += s_cnt[w * 256 + d0];
+        s_cnt[w * 256 + d0] = 0;
     }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int x = 1; x < 32; x <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, x);
+        if (lane >= x) incl += y;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    s_gbase[d0] = offs[(int64_t)d0 * nb + blockIdx.x];
     __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+    s_tstart[d0] = wpre + incl - tot;
+    __syncthreads();
+    // sweep 2: each item to its place in the tile's sorted order
     const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; ++it) {
         unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
         uint32_t d = dg[it];
         uint32_t before = 0;
-        if (d < 256u) before = s_cnt[warp][d];
+        if (d < 256u) before = s_cnt[warp * 256 + d];
         __syncwarp();
         if (d < 256u) {
-            if (lane == __ffs(peers) - 1) s_cnt[warp][d] = before + __popc(peers);
-            uint32_t pos = s_base[warp][d] + before + __popc(peers & lt_mask);
-            okeys[pos] = k[it];
-            ovals[pos] = v[it];
+            if (lane == __ffs(peers) - 1) s_cnt[warp * 256 + d] = before + __popc(peers);
+            const uint32_t lp = s_tstart[d] + s_base[warp * 256 + d] + before + __popc(peers & lt_mask);
+            s_k[lp] = k[it];
+            s_v[lp] = v[it];
         }
         __syncwarp();
+    }
+    __syncthreads();
+    // out in the tile's order: each digit's run lands contiguously
+    const int tile_n = (int)min((int64_t)RS_TILE, n - tile0);
+    for (int x = threadIdx.x; x < tile_n; x += RS_THREADS) {
+        const uint32_t key = s_k[x];
+        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t pos = s_gbase[d] + ((uint32_t)x - s_tstart[d]);
+        okeys[pos] = key;
+        ovals[pos] = s_v[x];
     }
 }
 
@@ -226,6 +261,7 @@ pastis_status radix_sort_u32_u64(pastis_ctx *c, uint32_t *keys, uint64_t *vals, 
     uint32_t *offs = hist + 256 * nb + 1;
     uint32_t *ik = keys, *ok = keys_alt;
     uint64_t *iv = vals, *ov = vals_alt;
+    if (c->prof_on) c->sort_passes += n * (int64_t)((key_bits + 7) / 8);
     for (int shift = 0; shift < key_bits; shift += 8) {
         prof_begin(c, "radix_hist");
         k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, c->stream>>>(ik, n, shift, hist, nb);
@@ -234,7 +270,7 @@ pastis_status radix_sort_u32_u64(pastis_ctx *c, uint32_t *keys, uint64_t *vals, 
         pastis_status st = exclusive_scan_u32(c, hist, offs, 256 * nb);
         if (st != PASTIS_OK) return st;
         prof_begin(c, "radix_scatter");
-        k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, c->stream>>>(ik, iv, n, shift, offs, nb, ok, ov);
+        k_rs_scatter<<<(unsigned)nb, RS_THREADS, RS_SCATTER_SMEM, c->stream>>>(ik, iv, n, shift, offs, nb, ok, ov);
         PASTIS_LAUNCHED(c);
         prof_end(c);
         uint32_t *tk = ik; ik = ok; ok = tk;
@@ -243,4 +279,8 @@ pastis_status radix_sort_u32_u64(pastis_ctx *c, uint32_t *keys, uint64_t *vals, 
     *keys_out = ik;
     *vals_out = iv;
     return PASTIS_OK;
+}
+
+cudaError_t radix_set_smem_limit() {
+    return cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SCATTER_SMEM);
 }

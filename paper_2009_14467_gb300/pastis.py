@@ -195,7 +195,8 @@ class Context:
         """pastis_ctx_stats: overlap-product work counted while profiling was on."""
         v = (ctypes.c_int64 * 4)()
         _check("pastis_ctx_stats", lib().pastis_ctx_stats(self.h, v, 4))
-        return {"spgemm_products": v[0], "spgemm_left_entries": v[1], "spgemm_records": v[2]}
+        return {"spgemm_products": v[0], "spgemm_left_entries": v[1], "spgemm_records": v[2],
+                "sort_element_passes": v[3]}
 
     def sw_layout(self) -> np.ndarray:
         """pastis_sw_layout_get: extra pass-1 stripes per query-length bin (uint8[64])."""

@@ -320,6 +320,9 @@ def test_profiler_counts_kernels(P, ctx):
             # every row but the last forms products over j > i)
             row_ptr, _, _ = O.kmers(O.encode(ps.ascii), ps.offsets, 6)
             assert st["spgemm_left_entries"] == int(row_ptr[-2])
+            # the sorts that build A: every residue's window by code (24^6 codes: four
+            # 8-bit passes), then the distinct k-mers by sequence (200 sequences: one)
+            assert st["sort_element_passes"] == 4 * int(ps.offsets[-1]) + int(row_ptr[-1])
 
 
 def test_spgemm_row_blocks_concatenate(P, ctx):
