@@ -111,3 +111,20 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_xd_roofline_peak_follows_the_lanes():
+    """The x-drop roofline divides by the measured 16x2 peak when the extensions run in
+    16-bit lanes and by the 32-bit peak otherwise; achieved = 11 ops per computed cell
+    over the launch time."""
+    cells, ms, n_sm, clk = 2.0e11, 500.0, 152, 2070.0
+    half_rate, word_rate = 3.2, 3.9
+    r16 = bench.xd_roofline(cells, ms, 4, half_rate, word_rate, n_sm, clk)
+    r32 = bench.xd_roofline(cells, ms, 0, half_rate, word_rate, n_sm, clk)
+    achieved = cells * bench.OPS_PER_CELL / (ms / 1000.0) / 1e12
+    assert r16["achieved"] == pytest.approx(achieved) and r32["achieved"] == pytest.approx(achieved)
+    assert r16["peak"] == pytest.approx(n_sm * half_rate * 32 * 2 * clk * 1e6 / 1e12)
+    assert r32["peak"] == pytest.approx(n_sm * word_rate * 32 * clk * 1e6 / 1e12)
+    assert r16["frac"] == pytest.approx(achieved / r16["peak"])
+    assert "4 extensions per warp" in r16["peak_note"] and "32-bit lanes" in r32["peak_note"]
+    assert r16["cells_per_clk_sm"] == pytest.approx(cells / (ms / 1000.0) / (n_sm * clk * 1e6))
