@@ -345,23 +345,24 @@ pastis_status pastis_autotune_sw(pastis_ctx *ctx, const uint8_t *d_qcodes, const
                                  int64_t *h_cycles);
 
 /* ---- batching: the x-drop lane layout -------------------------------------------------
- * The first phase of PASTIS_XD_FILTERED (the score, end and cells of every extension of
- * Sec. IV-E's x-drop, before the carried statistics) runs in 16-bit lanes with
- * `per_warp` extensions side by side in each warp (1, 2 or 4: one window of 128
- * diagonals over 32, 16 or 8 lanes), or in 32-bit lanes, one extension per warp
- * (per_warp = 0).  Extensions the 16-bit form cannot hold run in 32-bit lanes whatever
- * the setting: gap open or extend above 128, X above 30,000, the largest substitution
- * score times the shorter side of the extension above 30,000, a side of length 0, or a
- * computed antidiagonal wider than 64 cells.  A speed choice only: every output is the
- * same under every setting.  A context starts with PASTIS_XD_DEFAULT_PER_WARP.
+ * The extensions of Sec. IV-E's x-drop (PASTIS_XD: each with its carried statistics;
+ * PASTIS_XD_FILTERED: first every extension's score, end and cells, then the carried
+ * statistics of the seeds that may pass) run in 16-bit lanes with `per_warp`
+ * extensions side by side in each warp (1, 2 or 4: one window of 128 diagonals over 32,
+ * 16 or 8 lanes), or in 32-bit lanes, one extension per warp (per_warp = 0).
+ * Extensions the 16-bit form cannot hold run in 32-bit lanes whatever the setting: gap
+ * open or extend above 128, X above 30,000, the largest substitution score times the
+ * shorter side of the extension above 30,000, a side of length 0, or a computed
+ * antidiagonal wider than 64 cells.  A speed choice only: every output is the same
+ * under every setting.  A context starts with PASTIS_XD_DEFAULT_PER_WARP.
  * pastis_xd_layout_set gives PASTIS_ERR_INVALID_ARG for any other value and leaves the
  * setting unchanged; pastis_xd_layout_get returns it (-1 for a NULL context).        */
 #define PASTIS_XD_DEFAULT_PER_WARP 4
 pastis_status pastis_xd_layout_set(pastis_ctx *ctx, int32_t per_warp);
 int32_t pastis_xd_layout_get(const pastis_ctx *ctx);
 
-/* The x-drop layout tuner: runs the filter-only x-drop of the given pairs (the arguments
- * of pastis_align_pairs_qt; a sample of the workload's candidates) under each setting,
+/* The x-drop layout tuner: runs the x-drop of params->mode on the given pairs (the
+ * arguments of pastis_align_pairs_qt; a sample of the workload's candidates) under each setting,
  * 0, 1, 2 and 4, `reps` times each, every call timed by CUDA events on the context's
  * stream.  The fastest setting is set on the context when it beats the current one by
  * 2% or more (else the current one stays) and copied to *h_per_warp (optional); h_ms

@@ -299,8 +299,8 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
 }
 
 // ---------------------------------------------------------------------------------
-// The same extensions in 16-bit lanes, several per warp (the first phase of the
-// filter-only mode: score, end and cells, no carried statistics).
+// The same extensions in 16-bit lanes, several per warp, with or without the carried
+// statistics.
 //
 // The diagonal window of xd_diag_warp (128 diagonals, at most 64 computed cells per
 // antidiagonal) is split over G = 32 / R lanes, so a warp runs R extensions side by
@@ -332,12 +332,22 @@ __device__ bool xd_diag_warp(const uint8_t *q, int A, int qs, const uint8_t *t, 
 // nothing until it takes the next extension at the top of the loop.  The end cell is
 // found once per extension: the step that raises the best score keeps a copy of its
 // H registers, and the first row holding the best is read from that copy at the end.
+//
+// The carried statistics (identities and aligned columns along the path a traceback
+// from the cell would take, Sec. IV-E) are one 32-bit word per cell beside H, E and F,
+// for both parities.  A cell's words follow its winning predecessor: E and F take H's
+// (gap open) unless the extension wins outright, H takes the diagonal's plus one
+// column (and one identity when the residues match) unless F, then E, is strictly
+// larger.  Which candidate won is read off the packed results: a half of max(x, y)
+// equals x's exactly when x won or tied.  The score table then holds each score's byte
+// and the match bit (q == t) above it; the scores are sign-extended from the bytes.
 // ---------------------------------------------------------------------------------
 constexpr int XD16_NEG = -32512;                 // 0x8100
 constexpr uint32_t XD16_NEG2 = (uint32_t)(XD16_NEG & 0xffff) * 0x10001u;   // 0x81008100
 constexpr int XD16_LIM = 30000;                  // bound on X and on an extension's best score
 // Score table, int16: byte offset q * 1536 + (t >> 1) * 128 + (t & 1) * 2 + 4 * lane holds
-// s(q, t) for every lane, so lane L always reads bank L.
+// s(q, t) (with carries: the byte of s(q, t), then [q == t]) for every lane, so lane L
+// always reads bank L.
 constexpr int XD16_TAB = PASTIS_NSYM * PASTIS_NSYM * 32;   // entries
 constexpr uint32_t XD16_QOFF = PASTIS_NSYM / 2 * 128;      // bytes per query residue
 
@@ -345,6 +355,14 @@ constexpr uint32_t XD16_QOFF = PASTIS_NSYM / 2 * 128;      // bytes per query re
 static inline bool xd16_params_fit(int o, int e, int X) { return o <= 128 && e <= 128 && X <= XD16_LIM; }
 
 __device__ __forceinline__ uint32_t xd16_pk(int v) { return __byte_perm((uint32_t)v, 0u, 0x1010); }
+
+// The low bytes of a and b as two signed 16-bit halves: prmt in its default mode copies a
+// byte where a selector nibble has bit 3 clear and replicates its sign bit where it is set.
+__device__ __forceinline__ uint32_t xd16_sext_lo_bytes(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, 0xC480;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
 
 // Live bits of four cells in row order from the dead masks of two registers (halves of
 // 0xffff or 0): the high byte of each half, gathered in row order, then its top bit
@@ -354,11 +372,14 @@ __device__ __forceinline__ uint32_t xd16_live4(uint32_t dm0, uint32_t dm1) {
     return (x * 0x00204081u) >> 28;
 }
 
-template <int R>
+template <int R, bool C>
 struct xd16_ext {
     uint32_t H[2][R], E[2][R], F[2][R];          // [parity of the diagonals][register]
     uint32_t QW[R], TW[R];                       // cells 2r (low half), 2r + 1: table offsets of q and t
     uint32_t HS[R];                              // H of the antidiagonal sd that last raised best
+    // C: the carried statistics (identities << 16 | columns) of H, E and F, one word per
+    // cell [parity][register][half], and those of HS
+    uint32_t HC[2][C ? R : 1][2], EC[2][C ? R : 1][2], FC[2][C ? R : 1][2], HSC[C ? R : 1][2];
     const uint8_t *q, *t;
     int st, A, B;                                // A = B = 0 while the segment has no extension
     int d, best, sd, sa0, llo, lhi, kbase;
@@ -369,20 +390,20 @@ struct xd16_ext {
 
 // Table offset of query residue idx (0 outside the sequence), and of target residue idx
 // plus this lane's column.
-template <int R>
-__device__ __forceinline__ uint32_t xd16_qoff(const xd16_ext<R> &x, int idx) {
+template <int R, bool C>
+__device__ __forceinline__ uint32_t xd16_qoff(const xd16_ext<R, C> &x, int idx) {
     return (unsigned)idx < (unsigned)x.A ? (uint32_t)x.q[(long long)idx * x.st] * XD16_QOFF : 0u;
 }
-template <int R>
-__device__ __forceinline__ uint32_t xd16_toff(const xd16_ext<R> &x, int idx, uint32_t lane4) {
+template <int R, bool C>
+__device__ __forceinline__ uint32_t xd16_toff(const xd16_ext<R, C> &x, int idx, uint32_t lane4) {
     uint32_t c = (unsigned)idx < (unsigned)x.B ? (uint32_t)x.t[(long long)idx * x.st] : 0u;
     return (c >> 1) * 128u + (c & 1u) * 2u + lane4;
 }
 
 // The windows for antidiagonal d whose first row in this lane is a0: cell j has query
 // residue a0 + j - 1 and target residue d - a0 - j - 1.
-template <int R>
-__device__ __forceinline__ void xd16_load_windows(xd16_ext<R> &x, int d, int a0, uint32_t lane4) {
+template <int R, bool C>
+__device__ __forceinline__ void xd16_load_windows(xd16_ext<R, C> &x, int d, int a0, uint32_t lane4) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         x.QW[r] = xd16_qoff(x, a0 + 2 * r - 1) | (xd16_qoff(x, a0 + 2 * r) << 16);
@@ -392,8 +413,8 @@ __device__ __forceinline__ void xd16_load_windows(xd16_ext<R> &x, int d, int a0,
 
 // One antidiagonal (d = x.d + 1, of parity PAR) of the segment's extension, run by every
 // lane of the warp.
-template <int R, int PAR>
-__device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask, int sbase, const char *tab,
+template <int R, bool C, int PAR>
+__device__ __forceinline__ void xd16_step(xd16_ext<R, C> &x, int ls, unsigned smask, int sbase, const char *tab,
                                           uint32_t lane4, uint32_t o2, uint32_t ne2, int X, ext_out *out,
                                           uint32_t *ovf_list, uint32_t *ovf_n) {
     constexpr int G = 32 / R, WD = 4 * R, NC = 2 * R;
@@ -435,6 +456,17 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
                         x.H[p][r] = in ? h : XD16_NEG2;
                         x.E[p][r] = in ? ee : XD16_NEG2;
                         x.F[p][r] = in ? ff : XD16_NEG2;
+                        if constexpr (C) {
+#pragma unroll
+                            for (int hf = 0; hf < 2; ++hf) {
+                                const uint32_t hc = __shfl_sync(smask, x.HC[p][r][hf], src & (G - 1), G);
+                                const uint32_t ec = __shfl_sync(smask, x.EC[p][r][hf], src & (G - 1), G);
+                                const uint32_t fc = __shfl_sync(smask, x.FC[p][r][hf], src & (G - 1), G);
+                                x.HC[p][r][hf] = in ? hc : 0u;
+                                x.EC[p][r][hf] = in ? ec : 0u;
+                                x.FC[p][r][hf] = in ? fc : 0u;
+                            }
+                        }
                     }
                 a0 = (d + x.kbase + WD * ls + P) >> 1;
                 xd16_load_windows(x, d, a0, lane4);
@@ -445,14 +477,22 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
     const uint32_t lim2 = xd16_pk(lim), limm2 = __vsub2(lim2, 0x00010001u);
     const uint32_t span2 = xd16_pk(chi - clo), rb2 = xd16_pk(a0 - clo);
     // the sources on d - 1 that cross a lane boundary
-    uint32_t bh, bx;
+    uint32_t bh, bx, bhc = 0u, bxc = 0u;
     if (P == 0) {        // F of the first cell: the previous lane's last odd diagonal
         bh = __shfl_up_sync(0xffffffffu, x.H[Q][R - 1], 1, G);
         bx = __shfl_up_sync(0xffffffffu, x.F[Q][R - 1], 1, G);
+        if constexpr (C) {
+            bhc = __shfl_up_sync(0xffffffffu, x.HC[Q][R - 1][1], 1, G);
+            bxc = __shfl_up_sync(0xffffffffu, x.FC[Q][R - 1][1], 1, G);
+        }
         if (ls == 0) { bh = XD16_NEG2; bx = XD16_NEG2; }
     } else {             // E of the last cell: the next lane's first even diagonal
         bh = __shfl_down_sync(0xffffffffu, x.H[Q][0], 1, G);
         bx = __shfl_down_sync(0xffffffffu, x.E[Q][0], 1, G);
+        if constexpr (C) {
+            bhc = __shfl_down_sync(0xffffffffu, x.HC[Q][0][0], 1, G);
+            bxc = __shfl_down_sync(0xffffffffu, x.EC[Q][0][0], 1, G);
+        }
         if (ls == G - 1) { bh = XD16_NEG2; bx = XD16_NEG2; }
     }
     uint32_t dmk[R];                             // dead masks, for the live bits below
@@ -469,13 +509,42 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
             eh = __byte_perm(x.H[Q][r], r == R - 1 ? bh : x.H[Q][r + 1], 0x5432);
             ex = __byte_perm(x.E[Q][r], r == R - 1 ? bx : x.E[Q][r + 1], 0x5432);
         }
-        const uint32_t en = __viaddmax_s16x2(ex, ne2, __vsub2(eh, o2));
-        const uint32_t fn = __viaddmax_s16x2(fx, ne2, __vsub2(fh, o2));
+        const uint32_t eo = __vsub2(eh, o2), fo = __vsub2(fh, o2);
+        const uint32_t en = __viaddmax_s16x2(ex, ne2, eo);
+        const uint32_t fn = __viaddmax_s16x2(fx, ne2, fo);
         // substitution scores of rows a0 + 2r and a0 + 2r + 1 from this lane's table column
         const uint32_t ix = x.QW[r] + x.TW[r];
         const uint32_t s0 = *(const uint16_t *)(tab + (ix & 0xffffu));
         const uint32_t s1 = *(const uint16_t *)(tab + (ix >> 16));
-        const uint32_t hn = __vimax3_s16x2(__vadd2(x.H[P][r], __byte_perm(s0, s1, 0x5410)), en, fn);
+        // with carries an entry is the score's byte, then [q == t]: the scores sign-extended
+        const uint32_t dg = __vadd2(x.H[P][r], C ? xd16_sext_lo_bytes(s0, s1) : __byte_perm(s0, s1, 0x5410));
+        const uint32_t hn = __vimax3_s16x2(dg, en, fn);
+        if constexpr (C) {
+            // each cell's carries along the predecessor a traceback takes: E and F from H
+            // (the gap opens) on ties, H from the diagonal, then from F, then from E; a
+            // packed result equals the candidate it came from
+            const uint32_t xe = en ^ eo, xf = fn ^ fo, xdg = dg ^ hn, xfh = fn ^ hn;
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                auto zero = [hf](uint32_t v) { return hf ? (v >> 16) == 0u : (v & 0xffffu) == 0u; };
+                uint32_t ehc, exc, fhc, fxc;
+                if (P == 0) {
+                    ehc = x.HC[Q][r][hf]; exc = x.EC[Q][r][hf];
+                    fhc = hf ? x.HC[Q][r][0] : (r == 0 ? bhc : x.HC[Q][r > 0 ? r - 1 : 0][1]);
+                    fxc = hf ? x.FC[Q][r][0] : (r == 0 ? bxc : x.FC[Q][r > 0 ? r - 1 : 0][1]);
+                } else {
+                    fhc = x.HC[Q][r][hf]; fxc = x.FC[Q][r][hf];
+                    ehc = hf ? (r == R - 1 ? bhc : x.HC[Q][r < R - 1 ? r + 1 : 0][0]) : x.HC[Q][r][1];
+                    exc = hf ? (r == R - 1 ? bxc : x.EC[Q][r < R - 1 ? r + 1 : 0][0]) : x.EC[Q][r][1];
+                }
+                const uint32_t evc = zero(xe) ? ehc : exc;
+                const uint32_t fvc = zero(xf) ? fhc : fxc;
+                const uint32_t dvc = x.HC[P][r][hf] + 1u + (((hf ? s1 : s0) >> 8) << 16);
+                x.HC[P][r][hf] = zero(xdg) ? dvc : (zero(xfh) ? fvc : evc);
+                x.EC[P][r][hf] = evc;
+                x.FC[P][r][hf] = fvc;
+            }
+        }
         // dead halves: H < lim, or the row outside [clo, chi]
         const uint32_t rr = __vadd2(rb2, (uint32_t)((2 * r) | ((2 * r + 1) << 16)));
         const uint32_t w = __vmins2(rr, __vsub2(span2, rr));
@@ -507,7 +576,13 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
     for (int m = G / 2; m > 0; m >>= 1) toph = max(toph, __shfl_xor_sync(0xffffffffu, toph, m, G));
     const bool raise = !empty && !defer && toph > x.best;
 #pragma unroll
-    for (int r = 0; r < R; ++r) x.HS[r] = raise ? x.H[P][r] : x.HS[r];
+    for (int r = 0; r < R; ++r) {
+        x.HS[r] = raise ? x.H[P][r] : x.HS[r];
+        if constexpr (C) {
+            x.HSC[r][0] = raise ? x.HC[P][r][0] : x.HSC[r][0];
+            x.HSC[r][1] = raise ? x.HC[P][r][1] : x.HSC[r][1];
+        }
+    }
     x.sa0 = raise ? a0 : x.sa0;
     x.sd = raise ? d : x.sd;
     x.best = raise ? toph : x.best;
@@ -523,18 +598,28 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
             } else {
                 // the first row holding best on the antidiagonal that raised it last
                 unsigned mya = 0xFFFFFFFFu;
+                uint32_t myc = 0u;
 #pragma unroll
                 for (int j = NC - 1; j >= 0; --j) {
                     const uint32_t v = x.HS[j >> 1];
-                    if (((j & 1) ? (int)v >> 16 : (int)(short)(v & 0xffffu)) == x.best) mya = (unsigned)(x.sa0 + j);
+                    if (((j & 1) ? (int)v >> 16 : (int)(short)(v & 0xffffu)) == x.best) {
+                        mya = (unsigned)(x.sa0 + j);
+                        if constexpr (C) myc = x.HSC[j >> 1][j & 1];
+                    }
                 }
                 const int ta = (int)__reduce_min_sync(smask, mya);
+                uint32_t carry = 0u;
+                if constexpr (C) {
+                    // the carries of the lane that holds the end cell
+                    const unsigned who = __ballot_sync(smask, mya == (unsigned)ta);
+                    carry = __shfl_sync(smask, myc, (__ffs(who) - 1) & (G - 1), G);
+                }
                 if (ls == 0) {
                     ext_out res;
                     res.score = x.best;
                     res.a = x.best > 0 ? ta : 0;
                     res.b = x.best > 0 ? x.sd - ta : 0;
-                    res.carry = 0u;
+                    res.carry = x.best > 0 ? carry : 0u;
                     res.cells = x.cells;
                     out[x.task] = res;
                 }
@@ -546,16 +631,20 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R> &x, int ls, unsigned smask
     }
 }
 
-// The filter-only mode's first phase in 16-bit lanes: every task (4 p + 2 seed + left)
-// whose extension fits gets its score, end and cells; the others are listed in
-// ovf_list[*ovf_n] for k_xd_ext<false>.  smax = the largest substitution score.
-template <int R>
+// Extensions in 16-bit lanes: every task (4 p + 2 seed + left; with a task list the
+// listed ones, *d_ntask of them) whose extension fits gets its score, end and cells, and
+// with C its carried statistics; the others are listed in ovf_list[*ovf_n] for k_xd_ext.
+// smax = the largest substitution score.  Without C: the filter-only mode's first phase;
+// with C and a list: its second.
+template <int R, bool C>
 __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes, const int64_t *qoffsets,
                                                           const uint8_t *tcodes, const int64_t *toffsets,
                                                           const pastis_cand *pairs, int64_t n_pairs, int k,
                                                           const int8_t *gmat, int o, int e, int X, int smax,
                                                           int *next_task, ext_out *out, uint32_t *ovf_list,
-                                                          uint32_t *ovf_n, const int64_t *dn, const int *chk) {
+                                                          uint32_t *ovf_n, const uint32_t *task_list,
+                                                          const uint32_t *d_ntask, const int64_t *dn,
+                                                          const int *chk) {
     constexpr int G = 32 / R, WD = 4 * R;
     if (dn) n_pairs = *dn;
     if (chk && (chk[0] | chk[1])) return;
@@ -563,7 +652,8 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
     for (int i = threadIdx.x; i < XD16_TAB; i += blockDim.x) {
         // i = q * 768 + (t >> 1) * 64 + lane * 2 + (t & 1)
         const int q = i / 768, t = ((i % 768) >> 6) * 2 + (i & 1);
-        s_tab[i] = (uint16_t)(int)gmat[q * PASTIS_NSYM + t];
+        const int v = gmat[q * PASTIS_NSYM + t];
+        s_tab[i] = C ? (uint16_t)((v & 0xff) | (q == t ? 0x100 : 0)) : (uint16_t)v;
     }
     __syncthreads();
     const char *tab = (const char *)s_tab;
@@ -572,8 +662,8 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
     const int seg = lane / G, ls = lane % G, sbase = seg * G;
     const unsigned smask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << sbase);
     const uint32_t o2 = xd16_pk(o), ne2 = xd16_pk(-e);
-    const int64_t ntask = n_pairs * 4;
-    xd16_ext<R> x;
+    const int64_t ntask = task_list ? (int64_t)*d_ntask : n_pairs * 4;
+    xd16_ext<R, C> x;
     x.active = false;
     x.A = 0; x.B = 0; x.d = 0; x.best = 0; x.sd = 0; x.sa0 = 0; x.llo = 0; x.lhi = 0; x.kbase = -64; x.cells = 0;
     x.task = 0; x.st = 1; x.q = qcodes; x.t = tcodes;
@@ -581,6 +671,12 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
     for (int r = 0; r < R; ++r) {
         x.H[0][r] = x.H[1][r] = x.E[0][r] = x.E[1][r] = x.F[0][r] = x.F[1][r] = XD16_NEG2;
         x.QW[r] = 0u; x.TW[r] = lane4 | (lane4 << 16); x.HS[r] = XD16_NEG2;
+        if constexpr (C)
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                x.HC[0][r][hf] = x.HC[1][r][hf] = x.EC[0][r][hf] = x.EC[1][r][hf] = 0u;
+                x.FC[0][r][hf] = x.FC[1][r][hf] = x.HSC[r][hf] = 0u;
+            }
     }
     bool exhausted = false;
     for (;;) {
@@ -590,7 +686,7 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
                 if (ls == 0) slot = atomicAdd((unsigned long long *)next_task, 1ull);
                 slot = __shfl_sync(smask, slot, 0, G);
                 if ((int64_t)slot >= ntask) { exhausted = true; break; }
-                x.task = (int64_t)slot;
+                x.task = task_list ? (int64_t)task_list[slot] : (int64_t)slot;
                 const int64_t p = x.task >> 2;
                 const int seed = (int)((x.task >> 1) & 1), left = (int)(x.task & 1);
                 const pastis_cand c = pairs[p];
@@ -621,6 +717,11 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         x.H[pp][r] = XD16_NEG2; x.E[pp][r] = XD16_NEG2; x.F[pp][r] = XD16_NEG2;
+                        if constexpr (C)
+#pragma unroll
+                            for (int hf = 0; hf < 2; ++hf) {
+                                x.HC[pp][r][hf] = 0u; x.EC[pp][r][hf] = 0u; x.FC[pp][r][hf] = 0u;
+                            }
                     }
                 if (ls == 64 / WD) x.H[0][0] = XD16_NEG2 & 0xffff0000u;
                 x.d = 0; x.best = 0; x.sd = 0; x.sa0 = 0; x.llo = 0; x.lhi = 0; x.cells = 1;
@@ -629,8 +730,8 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
             }
         }
         if (__all_sync(0xffffffffu, exhausted)) break;
-        xd16_step<R, 1>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
-        xd16_step<R, 0>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
+        xd16_step<R, C, 1>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
+        xd16_step<R, C, 0>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
     }
 }
 
@@ -809,6 +910,41 @@ struct align_graph {
     int64_t qres_cap;      // capacity of the query residues
 };
 
+// The arguments of k_xd_ext16 that do not change between its launches.
+struct xd16_args {
+    const uint8_t *qcodes;
+    const int64_t *qoffsets;
+    const uint8_t *tcodes;
+    const int64_t *toffsets;
+    const pastis_cand *pairs;
+    int64_t n_pairs;
+    int k;
+    const int8_t *gmat;
+    int o, e, X, smax;
+    ext_out *out;
+    const int64_t *dn;
+    const int *chk;
+};
+
+template <int R, bool C>
+static void launch_xd16_r(pastis_ctx *ctx, const xd16_args &a, int *next_task, uint32_t *ovf_list, uint32_t *ovf_n,
+                          const uint32_t *task_list, const uint32_t *d_ntask) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<R, C>, ALN_THREADS, 0);
+    k_xd_ext16<R, C><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, ctx->stream>>>(
+        a.qcodes, a.qoffsets, a.tcodes, a.toffsets, a.pairs, a.n_pairs, a.k, a.gmat, a.o, a.e, a.X, a.smax, next_task,
+        a.out, ovf_list, ovf_n, task_list, d_ntask, a.dn, a.chk);
+}
+
+// k_xd_ext16 with per_warp (1, 2 or 4) extensions per warp, one CTA per resident slot.
+template <bool C>
+static void launch_xd16(pastis_ctx *ctx, int per_warp, const xd16_args &a, int *next_task, uint32_t *ovf_list,
+                        uint32_t *ovf_n, const uint32_t *task_list, const uint32_t *d_ntask) {
+    if (per_warp == 1) launch_xd16_r<1, C>(ctx, a, next_task, ovf_list, ovf_n, task_list, d_ntask);
+    else if (per_warp == 2) launch_xd16_r<2, C>(ctx, a, next_task, ovf_list, ovf_n, task_list, d_ntask);
+    else launch_xd16_r<4, C>(ctx, a, next_task, ovf_list, ovf_n, task_list, d_ntask);
+}
+
 static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const int64_t *d_qoffsets, int32_t n_q,
                               const uint8_t *d_tcodes, const int64_t *d_toffsets, int32_t n_t,
                               const pastis_cand *d_pairs, int64_t n_pairs, const pastis_params *params,
@@ -823,15 +959,15 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
     int8_t *dmat;
     PASTIS_WS(dmat, ctx, WS_FLAGS, 1024);
     int *flags = (int *)(dmat + 768);   // [0] error, [1] [3] [8] pair counters, [2] max length, [4] bad pair,
-                                        // [5] bad code, [6..7] [12..13] [14..15] task counters, [9] the
-                                        // 16-bit x-drop's deferred tasks
+                                        // [5] bad code, [6..7] [12..13] [14..15] [16..17] task counters,
+                                        // [9] [18] the 16-bit x-drop's deferred tasks (without, with carries)
     // the matrix, then the pass-1 layout at dmat + 640
     uint8_t hconst[640 + PASTIS_SW_BINS];
     memcpy(hconst, params->matrix, 576);
     memset(hconst + 576, 0, 64);
     memcpy(hconst + 640, ctx->sw_lay.extra, PASTIS_SW_BINS);
     if (!g) PASTIS_CUDA_TRY(cudaMemcpyAsync(dmat, hconst, sizeof(hconst), cudaMemcpyHostToDevice, st));
-    PASTIS_CUDA_TRY(cudaMemsetAsync(flags, 0, 64, st));
+    PASTIS_CUDA_TRY(cudaMemsetAsync(flags, 0, 80, st));
     const int xd = params->mode == PASTIS_XD || params->mode == PASTIS_XD_FILTERED;
     const int xd_filtered = params->mode == PASTIS_XD_FILTERED;
     const int64_t *dn = g ? g->dc : nullptr;
@@ -897,65 +1033,48 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
         PASTIS_WS(gbuf, ctx, WS_ALN_SCRATCH, sizeof(int32_t) * 18 * (size_t)W * nwarps);
         ext_out *ext;
         PASTIS_WS(ext, ctx, WS_ALN_PASS1, sizeof(ext_out) * 4 * (size_t)n_pairs);
+        const int64_t n4 = 4 * n_pairs;
+        uint32_t *need;
+        PASTIS_WS(need, ctx, WS_ALN_ORDER, sizeof(uint32_t) * (3 * (size_t)n4 + 4));
+        uint32_t *off = need + n4, *list = off + n4 + 1;
+        const int per_warp = ctx->xd_per_warp;
+        const bool lanes16 = per_warp && xd16_params_fit(params->gap_open, params->gap_extend, params->xdrop);
+        int smax = -64;
+        for (int x = 0; x < PASTIS_NSYM * PASTIS_NSYM; ++x) smax = std::max(smax, (int)params->matrix[x]);
+        const xd16_args a16{d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
+                            params->gap_open, params->gap_extend, params->xdrop, smax, ext, dn, chk};
         if (!xd_filtered) {
+            // every extension with carries: in 16-bit lanes where it fits (the others
+            // listed in list[flags[18]]), else in 32-bit lanes
             prof_begin(ctx, "xd_extend");
+            if (lanes16) {
+                launch_xd16<true>(ctx, per_warp, a16, flags + 16, list, (uint32_t *)(flags + 18), nullptr, nullptr);
+                PASTIS_LAUNCHED(ctx);
+            }
             k_xd_ext<true><<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
                                                            n_pairs, params->k, dmat, params->gap_open,
                                                            params->gap_extend, params->xdrop, gbuf, W, flags + 6, ext,
-                                                           nullptr, nullptr, dn, chk);
+                                                           lanes16 ? list : nullptr,
+                                                           lanes16 ? (uint32_t *)(flags + 18) : nullptr, dn, chk);
             PASTIS_LAUNCHED(ctx);
             prof_end(ctx);
         } else {
             // phase 1: every extension's score, end and cells; then the carried
             // statistics only for the seeds whose spans pass the coverage test
-            const int64_t n4 = 4 * n_pairs;
-            uint32_t *need;
-            PASTIS_WS(need, ctx, WS_ALN_ORDER, sizeof(uint32_t) * (3 * (size_t)n4 + 4));
-            uint32_t *off = need + n4, *list = off + n4 + 1;
-            const int per_warp = ctx->xd_per_warp;
-            if (per_warp && xd16_params_fit(params->gap_open, params->gap_extend, params->xdrop)) {
+            prof_begin(ctx, "xd_extend");
+            if (lanes16) {
                 // in 16-bit lanes, per_warp extensions per warp; the tasks it cannot hold
                 // are listed (list[flags[9]]) and run in 32-bit lanes
-                int smax = -64;
-                for (int x = 0; x < PASTIS_NSYM * PASTIS_NSYM; ++x) smax = std::max(smax, (int)params->matrix[x]);
-                uint32_t *ovf_n = (uint32_t *)(flags + 9);
-                int per_sm = 1;
-                prof_begin(ctx, "xd_extend");
-                if (per_warp == 1) {
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<1>, ALN_THREADS, 0);
-                    k_xd_ext16<1><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, st>>>(
-                        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
-                        params->gap_open, params->gap_extend, params->xdrop, smax, flags + 14, ext, list, ovf_n, dn,
-                        chk);
-                } else if (per_warp == 2) {
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<2>, ALN_THREADS, 0);
-                    k_xd_ext16<2><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, st>>>(
-                        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
-                        params->gap_open, params->gap_extend, params->xdrop, smax, flags + 14, ext, list, ovf_n, dn,
-                        chk);
-                } else {
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<4>, ALN_THREADS, 0);
-                    k_xd_ext16<4><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, st>>>(
-                        d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs, n_pairs, params->k, dmat,
-                        params->gap_open, params->gap_extend, params->xdrop, smax, flags + 14, ext, list, ovf_n, dn,
-                        chk);
-                }
+                launch_xd16<false>(ctx, per_warp, a16, flags + 14, list, (uint32_t *)(flags + 9), nullptr, nullptr);
                 PASTIS_LAUNCHED(ctx);
-                k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
-                                                                n_pairs, params->k, dmat, params->gap_open,
-                                                                params->gap_extend, params->xdrop, gbuf, W, flags + 6,
-                                                                ext, list, ovf_n, dn, chk);
-                PASTIS_LAUNCHED(ctx);
-                prof_end(ctx);
-            } else {
-                prof_begin(ctx, "xd_extend");
-                k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
-                                                                n_pairs, params->k, dmat, params->gap_open,
-                                                                params->gap_extend, params->xdrop, gbuf, W, flags + 6,
-                                                                ext, nullptr, nullptr, dn, chk);
-                PASTIS_LAUNCHED(ctx);
-                prof_end(ctx);
             }
+            k_xd_ext<false><<<blocks1, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
+                                                            n_pairs, params->k, dmat, params->gap_open,
+                                                            params->gap_extend, params->xdrop, gbuf, W, flags + 6,
+                                                            ext, lanes16 ? list : nullptr,
+                                                            lanes16 ? (uint32_t *)(flags + 9) : nullptr, dn, chk);
+            PASTIS_LAUNCHED(ctx);
+            prof_end(ctx);
             k_xd_mark<<<(unsigned)ceil_div64(n_pairs, 256), 256, 0, st>>>(d_qoffsets, d_toffsets, d_pairs, n_pairs,
                                                                           params->k, params->cov_min_pct, ext, need,
                                                                           dn, chk);
@@ -965,10 +1084,17 @@ static pastis_status align_qt(pastis_ctx *ctx, const uint8_t *d_qcodes, const in
             k_xd_tasks<<<(unsigned)ceil_div64(n4, 256), 256, 0, st>>>(need, off, n4, list);
             PASTIS_LAUNCHED(ctx);
             prof_begin(ctx, "xd_carry");
+            if (lanes16) {
+                // the flagged tasks (list[0 .. list[n4]) in 16-bit lanes with carries; the
+                // ones it cannot hold are listed in need[flags[18]], no longer needed
+                launch_xd16<true>(ctx, per_warp, a16, flags + 16, need, (uint32_t *)(flags + 18), list, list + n4);
+                PASTIS_LAUNCHED(ctx);
+            }
             k_xd_ext<true><<<blocks, ALN_THREADS, 0, st>>>(d_qcodes, d_qoffsets, d_tcodes, d_toffsets, d_pairs,
                                                            n_pairs, params->k, dmat, params->gap_open,
                                                            params->gap_extend, params->xdrop, gbuf, W, flags + 12,
-                                                           ext, list, list + n4, dn, chk);
+                                                           ext, lanes16 ? need : list,
+                                                           lanes16 ? (uint32_t *)(flags + 18) : list + n4, dn, chk);
             PASTIS_LAUNCHED(ctx);
             prof_end(ctx);
         }
@@ -1104,8 +1230,7 @@ extern "C" pastis_status pastis_autotune_xd(pastis_ctx *ctx, const uint8_t *d_qc
     if (n_pairs > 0) {
         pastis_aln *d_out;
         PASTIS_WS(d_out, ctx, WS_TUNE, sizeof(pastis_aln) * (size_t)n_pairs + 16);
-        pastis_params ps = *params;
-        ps.mode = PASTIS_XD_FILTERED;
+        const pastis_params &ps = *params;
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
             cudaGetLastError();

@@ -417,12 +417,13 @@ def _xd_mat(scale):
 @pytest.mark.parametrize("per_warp", [0, 1, 2, 4])
 @pytest.mark.parametrize("which", ["families", "wide", "edge_cases", "big_scores"])
 def test_xd_lanes_parity(P, ctx, per_warp, which):
-    """The filter-only x-drop's first phase in 16-bit lanes (1, 2 or 4 extensions per
-    warp) or in 32-bit lanes: every field against the oracle's mode 4.  'wide' (X = 1000)
-    grows computed antidiagonals past the 16-bit window, 'edge_cases' has seeds at
-    sequence ends (sides of length 0) and short sequences, 'big_scores' a matrix whose
-    scores times the extension length pass the 16-bit bound: those extensions run in
-    32-bit lanes, with identical results."""
+    """The x-drop in 16-bit lanes (1, 2 or 4 extensions per warp) or in 32-bit lanes,
+    both modes: the filter-only mode (its first phase without carried statistics, its
+    second with them) and the mode that carries them for every extension; every field
+    against the oracle's.  'wide' (X = 1000) grows computed antidiagonals past the
+    16-bit window, 'edge_cases' has seeds at sequence ends (sides of length 0) and short
+    sequences, 'big_scores' a matrix whose scores times the extension length pass the
+    16-bit bound: those extensions run in 32-bit lanes, with identical results."""
     mat, kw = MAT, {}
     if which == "edge_cases":
         ps = edge_case_set()
@@ -439,43 +440,46 @@ def test_xd_lanes_parity(P, ctx, per_warp, which):
             kw["xdrop"] = 1000
     assert len(cands) > 0
     codes = O.encode(ps.ascii)
-    params = P.Params(matrix=mat, mode=P.XD_FILTERED, **kw)
-    ctx.set_xd_layout(per_warp)
-    try:
-        cells = torch.zeros(1, dtype=torch.int64, device="cuda")
-        got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets),
-                                         dev(cands.view(np.uint8).reshape(-1, 20)), params, cells), P.ALN_DTYPE)
-    finally:
-        ctx.set_xd_layout()
-    want, wcells = O.align_pairs(codes, ps.offsets, cands, mat, params.gap_open, params.gap_extend, P.XD_FILTERED,
-                                 params.xdrop, params.k, params.ani_min_pct, params.cov_min_pct)
-    _cmp_alns(got, want)
-    assert int(cells.item()) == wcells
-
-
-@pytest.mark.parametrize("o,e,X", [(128, 1, 49), (129, 1, 49), (11, 1, 30000), (11, 1, 30001), (3, 1, 49),
-                                   (1, 1, 5), (40, 30, 49)])
-def test_xd_lanes_bounds(P, ctx, o, e, X):
-    """At and past the 16-bit kernel's bounds (gap open or extend 128 vs 129, X 30,000 vs
-    30,001) and with cheap or costly gaps (wide or narrow bands), every field of the
-    filter-only x-drop equals the oracle's, in 16-bit lanes (four per warp) and in 32-bit
-    lanes."""
-    ps = synth.families_1k().subset(np.arange(400))
-    cands = _cands(P, ctx, ps)[1]
-    codes = O.encode(ps.ascii)
-    params = P.Params(matrix=MAT, mode=P.XD_FILTERED, gap_open=o, gap_extend=e, xdrop=X)
-    want, wcells = O.align_pairs(codes, ps.offsets, cands, MAT, o, e, P.XD_FILTERED, X, params.k,
-                                 params.ani_min_pct, params.cov_min_pct)
-    for pw in (4, 0):
-        ctx.set_xd_layout(pw)
+    for mode in (P.XD_FILTERED, P.XD):
+        params = P.Params(matrix=mat, mode=mode, **kw)
+        ctx.set_xd_layout(per_warp)
         try:
             cells = torch.zeros(1, dtype=torch.int64, device="cuda")
             got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets),
                                              dev(cands.view(np.uint8).reshape(-1, 20)), params, cells), P.ALN_DTYPE)
         finally:
             ctx.set_xd_layout()
+        want, wcells = O.align_pairs(codes, ps.offsets, cands, mat, params.gap_open, params.gap_extend, mode,
+                                     params.xdrop, params.k, params.ani_min_pct, params.cov_min_pct)
         _cmp_alns(got, want)
         assert int(cells.item()) == wcells
+
+
+@pytest.mark.parametrize("o,e,X", [(128, 1, 49), (129, 1, 49), (11, 1, 30000), (11, 1, 30001), (3, 1, 49),
+                                   (1, 1, 5), (40, 30, 49)])
+def test_xd_lanes_bounds(P, ctx, o, e, X):
+    """At and past the 16-bit kernel's bounds (gap open or extend 128 vs 129, X 30,000 vs
+    30,001) and with cheap or costly gaps (wide or narrow bands), every field of both
+    x-drop modes equals the oracle's, in 16-bit lanes (four per warp) and in 32-bit
+    lanes."""
+    ps = synth.families_1k().subset(np.arange(400))
+    cands = _cands(P, ctx, ps)[1]
+    codes = O.encode(ps.ascii)
+    for mode in (P.XD_FILTERED, P.XD):
+        params = P.Params(matrix=MAT, mode=mode, gap_open=o, gap_extend=e, xdrop=X)
+        want, wcells = O.align_pairs(codes, ps.offsets, cands, MAT, o, e, mode, X, params.k,
+                                     params.ani_min_pct, params.cov_min_pct)
+        for pw in (4, 0):
+            ctx.set_xd_layout(pw)
+            try:
+                cells = torch.zeros(1, dtype=torch.int64, device="cuda")
+                got = P.to_records(P.align_pairs(ctx, dev(codes), dev(ps.offsets),
+                                                 dev(cands.view(np.uint8).reshape(-1, 20)), params, cells),
+                                   P.ALN_DTYPE)
+            finally:
+                ctx.set_xd_layout()
+            _cmp_alns(got, want)
+            assert int(cells.item()) == wcells
 
 
 def test_xd_layout_setting(P, ctx):
