@@ -634,21 +634,17 @@ __device__ __forceinline__ void xd16_step(xd16_ext<R, C> &x, int ls, unsigned sm
 // Extensions in 16-bit lanes: every task (4 p + 2 seed + left; with a task list the
 // listed ones, *d_ntask of them) whose extension fits gets its score, end and cells, and
 // with C its carried statistics; the others are listed in ovf_list[*ovf_n] for k_xd_ext.
-// smax = the largest substitution score.  Without C: the filter-only mode's first phase;
-// with C and a list: its second.
+// smax = the largest substitution score; s_tab = the CTA's score table.
 template <int R, bool C>
-__global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes, const int64_t *qoffsets,
-                                                          const uint8_t *tcodes, const int64_t *toffsets,
-                                                          const pastis_cand *pairs, int64_t n_pairs, int k,
-                                                          const int8_t *gmat, int o, int e, int X, int smax,
-                                                          int *next_task, ext_out *out, uint32_t *ovf_list,
-                                                          uint32_t *ovf_n, const uint32_t *task_list,
-                                                          const uint32_t *d_ntask, const int64_t *dn,
-                                                          const int *chk) {
+__device__ __forceinline__ void xd16_run(const uint8_t *qcodes, const int64_t *qoffsets, const uint8_t *tcodes,
+                                         const int64_t *toffsets, const pastis_cand *pairs, int64_t n_pairs, int k,
+                                         const int8_t *gmat, int o, int e, int X, int smax, int *next_task,
+                                         ext_out *out, uint32_t *ovf_list, uint32_t *ovf_n,
+                                         const uint32_t *task_list, const uint32_t *d_ntask, const int64_t *dn,
+                                         const int *chk, uint16_t *s_tab) {
     constexpr int G = 32 / R, WD = 4 * R;
     if (dn) n_pairs = *dn;
     if (chk && (chk[0] | chk[1])) return;
-    __shared__ uint16_t s_tab[XD16_TAB];
     for (int i = threadIdx.x; i < XD16_TAB; i += blockDim.x) {
         // i = q * 768 + (t >> 1) * 64 + lane * 2 + (t & 1)
         const int q = i / 768, t = ((i % 768) >> 6) * 2 + (i & 1);
@@ -734,6 +730,36 @@ __global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(const uint8_t *qcodes,
         xd16_step<R, C, 0>(x, ls, smask, sbase, tab, lane4, o2, ne2, X, out, ovf_list, ovf_n);
     }
 }
+
+
+#define XD16_PARAMS                                                                                         \
+    const uint8_t *qcodes, const int64_t *qoffsets, const uint8_t *tcodes, const int64_t *toffsets,         \
+        const pastis_cand *pairs, int64_t n_pairs, int k, const int8_t *gmat, int o, int e, int X, int smax, \
+        int *next_task, ext_out *out, uint32_t *ovf_list, uint32_t *ovf_n, const uint32_t *task_list,       \
+        const uint32_t *d_ntask, const int64_t *dn, const int *chk
+#define XD16_ARGS                                                                                        \
+    qcodes, qoffsets, tcodes, toffsets, pairs, n_pairs, k, gmat, o, e, X, smax, next_task, out, ovf_list, \
+        ovf_n, task_list, d_ntask, dn, chk
+
+// Without carries: the filter-only mode's first phase (at most 79 registers: three CTAs
+// per SM).
+template <int R>
+__global__ void __launch_bounds__(ALN_THREADS) k_xd_ext16(XD16_PARAMS) {
+    __shared__ uint16_t s_tab[XD16_TAB];
+    xd16_run<R, false>(XD16_ARGS, s_tab);
+}
+
+// With carries: the filter-only mode's second phase (over its task list) and PASTIS_XD.
+// Held to two CTAs per SM: with four extensions per warp the words take 150 registers
+// unbounded (one CTA), 128 with a few spilled, and the second occupancy pays more than
+// the spills cost.
+template <int R>
+__global__ void __launch_bounds__(ALN_THREADS, 2) k_xd_ext16_carry(XD16_PARAMS) {
+    __shared__ uint16_t s_tab[XD16_TAB];
+    xd16_run<R, true>(XD16_ARGS, s_tab);
+}
+#undef XD16_PARAMS
+#undef XD16_ARGS
 
 // Extension tasks: task = 4 p + 2 seed + left.  With a task list the kernel runs only
 // the listed tasks (*d_ntask of them): the second phase of the filter-only mode.
@@ -910,7 +936,7 @@ struct align_graph {
     int64_t qres_cap;      // capacity of the query residues
 };
 
-// The arguments of k_xd_ext16 that do not change between its launches.
+// The arguments of k_xd_ext16 / k_xd_ext16_carry that do not change between their launches.
 struct xd16_args {
     const uint8_t *qcodes;
     const int64_t *qoffsets;
@@ -930,13 +956,15 @@ template <int R, bool C>
 static void launch_xd16_r(pastis_ctx *ctx, const xd16_args &a, int *next_task, uint32_t *ovf_list, uint32_t *ovf_n,
                           const uint32_t *task_list, const uint32_t *d_ntask) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xd_ext16<R, C>, ALN_THREADS, 0);
-    k_xd_ext16<R, C><<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, ctx->stream>>>(
+    auto kern = C ? k_xd_ext16_carry<R> : k_xd_ext16<R>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ALN_THREADS, 0);
+    kern<<<ctx->sm_count * std::max(per_sm, 1), ALN_THREADS, 0, ctx->stream>>>(
         a.qcodes, a.qoffsets, a.tcodes, a.toffsets, a.pairs, a.n_pairs, a.k, a.gmat, a.o, a.e, a.X, a.smax, next_task,
         a.out, ovf_list, ovf_n, task_list, d_ntask, a.dn, a.chk);
 }
 
-// k_xd_ext16 with per_warp (1, 2 or 4) extensions per warp, one CTA per resident slot.
+// k_xd_ext16 (C: k_xd_ext16_carry) with per_warp (1, 2 or 4) extensions per warp, one CTA
+// per resident slot.
 template <bool C>
 static void launch_xd16(pastis_ctx *ctx, int per_warp, const xd16_args &a, int *next_task, uint32_t *ovf_list,
                         uint32_t *ovf_n, const uint32_t *task_list, const uint32_t *d_ntask) {
