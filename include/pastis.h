@@ -61,7 +61,7 @@ enum {
     PASTIS_ERR_OUT_OF_MEMORY = 4,    /* workspace allocation failed                        */
     PASTIS_ERR_CUDA = 5,             /* a CUDA runtime call failed                          */
     PASTIS_ERR_TIMEOUT = 6,          /* a bounded device-side wait ran out                 */
-    PASTIS_ERR_UNSUPPORTED = 7,      /* a valid request this build does not implement      */
+    PASTIS_ERR_UNSUPPORTED = 7,      /* a valid request this library does not implement    */
     PASTIS_ERR_INTERNAL = 8          /* a device-side consistency check failed             */
 };
 
